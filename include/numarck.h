@@ -1,0 +1,254 @@
+/*
+ * numarck.h — C ABI of the GB300 NUMARCK compression hot path.
+ *
+ * NUMARCK (Yuan et al., "Parallel Implementation of Lossy Data Compression for Temporal
+ * Data Sets", arXiv 1703.02438) compresses a timestep of a variable against the previous
+ * timestep of the same variable:
+ *
+ *   1. change ratios      d_j = (cur_j - prev_j) / prev_j                 (Eq. 1, §III.A)
+ *   2. top-k binning      bins of width 2E over the ratios, histogram, keep the
+ *                         k = 2^B - 1 most populated bins                  (§IV.B.1)
+ *   3. indexing           each point gets the B-bit id of its selected bin, or the
+ *                         marker 2^B - 1 ("incompressible"), whose value is stored as is
+ *                                                                          (§III.C, §IV.C)
+ *   4. decompression      R_j = prev_j * (1 + centre[idx_j]), or the stored value
+ *                                                                          (Eq. 4, §III.E)
+ *   5. partial decompression of a segment via per-block offset tables       (§IV.C, §V.C)
+ *
+ * Conventions for every entry point:
+ *   - All data pointers (prev, cur, blob, workspace, out) are DEVICE pointers owned by the
+ *     caller. The library never allocates device memory and never frees caller memory.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy default stream).
+ *     No entry point synchronises the stream except where stated ("synchronous").
+ *   - Argument errors are detected on the host before any launch, and the call then
+ *     returns without touching device memory. Errors found on the device during
+ *     compression are written to the blob header's `status` word (read it with
+ *     numarck_blob_size after the stream has been synchronised).
+ *   - The element type T is float (dtype NUMARCK_F32) or double (NUMARCK_F64); L = sizeof(T).
+ *     All method arithmetic is done in T with IEEE round-to-nearest-even and no fused
+ *     multiply-add, in the order stated in the blob format description below, so that the
+ *     output is a deterministic function of the inputs (independent of launch shape).
+ *   - Multi-byte fields are little-endian.
+ */
+#ifndef NUMARCK_H
+#define NUMARCK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque CUDA stream handle; identical to cudaStream_t / CUstream. */
+typedef struct CUstream_st* numarck_stream_t;
+
+/* ---- status codes (return value of every int-returning entry point) ---- */
+#define NUMARCK_OK               0
+#define NUMARCK_ERR_INVALID_ARG  1  /* bad pointer, size, E, B, dtype, anchor or block size */
+#define NUMARCK_ERR_CAPACITY     2  /* blob or workspace buffer smaller than required       */
+#define NUMARCK_ERR_CUDA         3  /* a CUDA runtime call or kernel launch failed           */
+#define NUMARCK_ERR_CORRUPT      4  /* blob header inconsistent (magic, version, fields)     */
+#define NUMARCK_ERR_RANGE        5  /* decompress range outside [0, n]                       */
+#define NUMARCK_ERR_TIMEOUT      6  /* a bounded device-side wait gave up                    */
+#define NUMARCK_ERR_NOMEM        7  /* host-side allocation failed                           */
+
+/* ---- element types and grid anchors ---- */
+#define NUMARCK_F32 0
+#define NUMARCK_F64 1
+
+/* Grid origin of the top-k bins (the paper says the ratio range is divided into bins of
+ * width 2E, §IV.B.1, and that the global min/max ratio is "used in the bin construction
+ * phase", §IV.A, but never states where the first edge lies):
+ *   NUMARCK_ANCHOR_ZERO  edges at a + b*2E with a = -E: bin 0 is centred on ratio 0, so
+ *                        unchanged points reconstruct exactly (default; no extra pass).
+ *   NUMARCK_ANCHOR_MIN   a = the minimum binnable ratio (the paper's literal reading;
+ *                        costs one extra pass over both timesteps). */
+#define NUMARCK_ANCHOR_ZERO 0
+#define NUMARCK_ANCHOR_MIN  1
+
+/* ---- format constants ---- */
+#define NUMARCK_MAGIC          0x314B4D4Eu   /* "NMK1" */
+#define NUMARCK_VERSION        1u
+#define NUMARCK_HEADER_BYTES   256           /* fixed header at the start of every blob   */
+#define NUMARCK_SECTION_ALIGN  256           /* every section starts at a multiple of it  */
+#define NUMARCK_SUB_BLOCK      4096          /* elements per sub-block (see sub_off below) */
+#define NUMARCK_WINDOW_LOG2    21            /* binnable iff |ratio| <= 2^21 * 2E          */
+#define NUMARCK_MAX_B          16
+#define NUMARCK_DEFAULT_BLOCK_BYTES (1 << 20) /* 1 MB index blocks, as in the paper's runs */
+
+/* Compression parameters (user-controllable parameters of §IV.B.2 and §IV.C). */
+typedef struct numarck_params {
+  int32_t dtype;        /* NUMARCK_F32 or NUMARCK_F64                                     */
+  int32_t B;            /* index bits, 1..16; k = 2^B - 1 bins, marker M = 2^B - 1         */
+  double  E;            /* error bound, 2^-60 <= E < 1; bin width is 2E (§IV.B.1)          */
+  int32_t anchor;       /* NUMARCK_ANCHOR_ZERO or NUMARCK_ANCHOR_MIN                      */
+  int32_t reserved;     /* must be 0                                                       */
+  int64_t block_bytes;  /* index-table block size in bytes, 16..2^30; 0 = the 1 MB default */
+} numarck_params;
+
+/*
+ * ---- Blob format (version 1) ----
+ *
+ * A compressed timestep is one contiguous byte buffer ("blob") holding the arrays of the
+ * paper's file layout (§IV.D, Fig. 2): bin centres, the index-table offset table, the
+ * incompressible offset table, the big index table and the incompressible table. It adds a
+ * fixed header and a sub-block offset table. Sections start at multiples of 256 bytes; all
+ * bytes between sections and all padding are zero, so a blob is a pure function of
+ * (prev, cur, params).
+ *
+ *   [0, 256)          header (numarck_header below)
+ *   off_centres       T centres[2^B]        centre of the bin with index r (r < n_sel);
+ *                                           0 for r >= n_sel (Fig. 2 "bin_centers", 2^B
+ *                                           entries, §III.B)
+ *   off_idx_off       int64 idx_off[nblocks+1]  byte offset of index block q inside the
+ *                                           index section; idx_off[nblocks] = its size (§IV.C)
+ *   off_inc_off       int64 inc_off[nblocks+1]  incompressible points in blocks < q;
+ *                                           inc_off[nblocks] = n_inc (§IV.C)
+ *   off_sub_off       int64 sub_off[nsub]   incompressible points before sub-block g
+ *                                           (global count; sub-blocks below)
+ *   off_index         index blocks          block q holds the indices of elements
+ *                                           [q*epb, min(n, (q+1)*epb)), epb =
+ *                                           floor(8*block_bytes / B) (§IV.C); index i of the
+ *                                           block occupies bits [i*B, i*B+B) of the block,
+ *                                           least significant index bit first, and bit t of
+ *                                           the block is bit (t mod 8) of byte t/8. A block
+ *                                           is ceil(count*B/8) bytes followed by zero bytes
+ *                                           up to a multiple of 16; block q starts at
+ *                                           q * block_stride, block_stride =
+ *                                           round_up(ceil(epb*B/8), 16).
+ *   off_exact         T exact[n_inc]        the values cur_j of the points with index M, in
+ *                                           ascending j, bit-for-bit (§III.C)
+ *   total_bytes       = off_exact + n_inc * L
+ *
+ * Sub-blocks: block q is split into ceil(count_q / 4096) sub-blocks of 4096 elements (the
+ * last one of a block may be shorter); they are numbered globally in element order,
+ * nsub in total. sub_off lets a decoder start at any sub-block without scanning the block
+ * (the paper stores only the per-block table, §IV.C; the extra table costs 8 bytes per
+ * 4096 elements).
+ *
+ * Method arithmetic (all in T, RNE, no FMA), with E_T = (T)E:
+ *   w = E_T + E_T;  inv_w = 1 / w;  cap = w * 2^21
+ *   ratio_j = (cur_j - prev_j) / prev_j                                   (Eq. 1)
+ *   binnable_j = ratio_j finite and |ratio_j| <= cap
+ *   a = -E_T (ANCHOR_ZERO) | min over binnable ratios, 0 if none (ANCHOR_MIN)
+ *   bin_j = floor((ratio_j - a) * inv_w)                                  (§IV.B.1)
+ *   histogram over the bins of binnable points; S = the min(k, #non-empty) bins with the
+ *   largest counts, ties broken by the smaller bin; index r of a selected bin = its position
+ *   in S sorted by ascending bin                                          (§IV.B.1)
+ *   centre_r = a + (((T)bin_r + 0.5) * w);  m_r = 1 + centre_r
+ *   idx_j = r if binnable, bin_j in S and |(prev_j * m_r) - cur_j| <= E_T * |cur_j|,
+ *           else M                                                        (§III.C)
+ *   decompression: R_j = idx_j == M ? exact[next] : prev_j * (1 + centre[idx_j])  (Eq. 4)
+ */
+typedef struct numarck_header {
+  uint32_t magic;        /*   0: NUMARCK_MAGIC                                   */
+  uint32_t version;      /*   4: NUMARCK_VERSION                                 */
+  int32_t  dtype;        /*   8                                                  */
+  int32_t  B;            /*  12                                                  */
+  double   E;            /*  16: E as passed in numarck_params                   */
+  int32_t  anchor;       /*  24                                                  */
+  int32_t  status;       /*  28: 0, or a NUMARCK_ERR_* code set on the device    */
+  int64_t  n;            /*  32: elements                                        */
+  int64_t  block_bytes;  /*  40                                                  */
+  int64_t  epb;          /*  48: elements per index block (Fig. 2 "elements_per_block") */
+  int64_t  nblocks;      /*  56                                                  */
+  int64_t  sub;          /*  64: NUMARCK_SUB_BLOCK                               */
+  int64_t  nsub;         /*  72                                                  */
+  int64_t  n_sel;        /*  80: selected bins |S| <= 2^B - 1                    */
+  int64_t  n_inc;        /*  88: incompressible points                           */
+  double   a;            /*  96: grid anchor (the T value, widened exactly)      */
+  int64_t  block_stride; /* 104                                                  */
+  int64_t  off_centres;  /* 112                                                  */
+  int64_t  off_idx_off;  /* 120                                                  */
+  int64_t  off_inc_off;  /* 128                                                  */
+  int64_t  off_sub_off;  /* 136                                                  */
+  int64_t  off_index;    /* 144                                                  */
+  int64_t  off_exact;    /* 152                                                  */
+  int64_t  total_bytes;  /* 160                                                  */
+  uint8_t  reserved[88]; /* 168: zero                                            */
+} numarck_header;
+
+/* ---- sizing (host only; never touch the device) ---- */
+
+/* Bytes a blob can need for n elements: every section sized for the worst case n_inc = n.
+ * Returns 0 if n or *p is invalid. */
+size_t numarck_compress_bound(int64_t n, const numarck_params* p);
+
+/* Bytes of device workspace numarck_compress needs for n elements (histogram window of
+ * 2^22 + 16 bins, rank table, per-sub-block scan state). Returns 0 if invalid. */
+size_t numarck_workspace_bytes(int64_t n, const numarck_params* p);
+
+/* Zero-fills a workspace (asynchronous on stream). A workspace must be zero-filled once
+ * before its first use; every later numarck_compress call leaves it ready for the next
+ * one, so it is initialised once and reused. Returns NUMARCK_ERR_INVALID_ARG for a NULL
+ * pointer, NUMARCK_ERR_CUDA if the memset cannot be queued. */
+int numarck_workspace_init(void* ws, size_t ws_bytes, numarck_stream_t stream);
+
+/* ---- compression (§III.A-C, §IV.A-C) ----
+ *
+ * prev, cur : device arrays of n elements of T (any alignment; 16-byte aligned is faster).
+ *             prev is the timestep the decompressor will hold: in a chain of timesteps pass
+ *             the previous reconstruction so that errors do not accumulate (Eq. 4 uses
+ *             R_{i-1}).
+ * n         : 0 <= n <= 2^40.
+ * p         : parameters (host pointer).
+ * blob      : device buffer of blob_cap >= numarck_compress_bound(n, p) bytes, 256-byte
+ *             aligned. On completion it holds the blob; bytes past total_bytes are undefined.
+ * ws        : device workspace of ws_bytes >= numarck_workspace_bytes(n, p), 256-byte
+ *             aligned, zero-filled before first use (numarck_workspace_init). Two calls
+ *             that overlap in time must not share a workspace.
+ * stream    : the stream the work is queued on.
+ * Returns NUMARCK_OK once the work is queued (host-side errors as listed above). */
+int numarck_compress(const void* prev, const void* cur, int64_t n, const numarck_params* p,
+                     void* blob, size_t blob_cap, void* ws, size_t ws_bytes,
+                     numarck_stream_t stream);
+
+/* ---- header inspection (host only) ----
+ * header_host: a HOST copy of (at least) the first NUMARCK_HEADER_BYTES bytes of a blob,
+ * taken after the compressing stream has been synchronised.
+ * numarck_blob_size: on success stores total_bytes; returns the device status word if it is
+ *   non-zero, NUMARCK_ERR_CORRUPT if magic/version/fields are inconsistent.
+ * numarck_read_header: validates and copies the header into *out. */
+int numarck_blob_size(const void* header_host, size_t* bytes);
+int numarck_read_header(const void* header_host, numarck_header* out);
+
+/* ---- decompression (Eq. 4, §III.E) ----
+ * blob        : device pointer to a complete blob.
+ * header_host : host copy of its header (NUMARCK_HEADER_BYTES), or NULL; with NULL the
+ *               call copies the header from the device and synchronises the stream first
+ *               (synchronous).
+ * prev        : device array of n elements of T, the same prev the blob was compressed
+ *               against.
+ * out         : device array of n elements of T; receives the reconstruction. Must not
+ *               overlap prev or blob.
+ * n           : must equal the header's n.
+ * status_dev  : optional device int32; if non-NULL the kernels store a NUMARCK_ERR_* code
+ *               into it when the blob's offset tables are inconsistent with its index table
+ *               (it is not cleared on success). May be NULL.
+ */
+int numarck_decompress(const void* blob, const void* header_host, const void* prev,
+                       void* out, int64_t n, int32_t* status_dev, numarck_stream_t stream);
+
+/* ---- partial decompression (§IV.C, §V.C) ----
+ * Reconstructs elements [start, start+count) only, touching the index blocks and exact
+ * values of that segment.
+ * prev_seg : device array of count elements = prev[start : start+count].
+ * out_seg  : device array of count elements; receives R[start : start+count].
+ * Returns NUMARCK_ERR_RANGE unless 0 <= start <= start+count <= n.
+ * The result equals the same slice of numarck_decompress's output, bit for bit. */
+int numarck_decompress_range(const void* blob, const void* header_host,
+                             const void* prev_seg, int64_t start, int64_t count,
+                             void* out_seg, int32_t* status_dev, numarck_stream_t stream);
+
+/* Human-readable name of a status code (static string). */
+const char* numarck_status_string(int code);
+
+/* Library version string, e.g. "numarck-gb300 1 sm_103a". */
+const char* numarck_version(void);
+
+#ifdef __cplusplus
+}  /* extern "C" */
+#endif
+
+#endif /* NUMARCK_H */
