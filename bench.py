@@ -1,0 +1,412 @@
+#!/usr/bin/env python3
+"""NUMARCK compress + decompress throughput on GB300.
+
+Workload (default, the configuration the headline metric is quoted on): a FLASH-like 3-D float64
+density field of 1024^3 cells (8 GiB per timestep), 4 consecutive timesteps compressed pairwise
+in a closed loop (prev = previous reconstruction), for every E in {1e-3, 1e-4} and B in {8, 10}.
+One step = those 12 (pair, E, B) compressions and their 12 decompressions. Inputs are 8 GiB
+arrays, far larger than the 129 MB L2, so no L2 flush is needed between iterations.
+
+value = input bytes (n * 8 per pair, once for compression and once for decompression counted as
+one pass of the variable) / (compress time + decompress time), i.e. n*L / (t_c + t_d) summed
+over the step, in GB/s of the uncompressed variable, on the device with CUDA events.
+
+--impl reference times the CPU oracle (plain numpy, one host core) on a bounded sample of the
+same workload; it is the reference arm of this comparison (the paper has no GPU code).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+COMBOS = [(1e-3, 8), (1e-3, 10), (1e-4, 8), (1e-4, 10)]
+METRIC = "compress+decompress input GB/s (and % of HBM peak) on 1 GB300, bit-exact vs oracle"
+WORKLOAD = ("FLASH-like 3-D float64 field 1024^3 (8 GiB/step), 4 timesteps, 3 closed-loop pairs "
+            "x E{1e-3,1e-4} x B{8,10}")
+KERNEL_FILES = {"k3_assign": ["k_assign.cu", "common.cuh"],
+                "k1_hist": ["k_hist.cu", "common.cuh"],
+                "k4_decode": ["k_decode.cu", "common.cuh"]}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="numarck", choices=["numarck", "reference"])
+    ap.add_argument("--side", type=int, default=1024, help="grid side (1024 = the full workload)")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=1 << 24,
+                    help="elements of the oracle's bounded sample")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------------------
+def _rank_world():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+
+
+def _init_dist(world):
+    import torch
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return dist if world > 1 else None
+
+
+def _barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def _max_over_ranks(dist, v: float) -> float:
+    if dist is None:
+        return v
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sum_over_ranks(dist, v: float) -> float:
+    if dist is None:
+        return v
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index),
+                                       f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "samples": len(rows),
+                "reasons": sorted(reasons)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def _kernel_hash(kernel: str) -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_FILES[kernel]:
+        with open(os.path.join(ROOT, "paper_1703_02438_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel: str, side: int):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    kernel source; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tr = json.load(f)
+        e = tr[kernel]
+        if e.get("source_sha") != _kernel_hash(kernel):
+            return None
+        return float(e["bytes_per_launch_full"]) * (side ** 3) / float(e["n_full"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# ----------------------------------------------------------------------------------------
+def cpu_oracle_sample(pair, sample: int):
+    """The oracle as it stands, on `sample` contiguous elements of pair (x1 -> x2) at E=1e-3,
+    B=8: compress + decompress; returns (GB/s of input, seconds, description)."""
+    from oracle import numarck_oracle as O
+    p, x = pair
+    n = min(sample, p.numel())
+    lo = (p.numel() - n) // 2
+    ps = p[lo: lo + n].cpu().numpy().copy()
+    xs = x[lo: lo + n].cpu().numpy().copy()
+    t0 = time.perf_counter()
+    blob = O.compress(ps, xs, 1e-3, 8).to_bytes()
+    t1 = time.perf_counter()
+    O.decompress(blob, ps)
+    t2 = time.perf_counter()
+    gbs = n * ps.itemsize / (t2 - t0) / 1e9
+    return gbs, t2 - t0, (f"{n} contiguous float64 elements (middle of timestep pair 1->2), "
+                          f"E=1e-3 B=8, compress {t1 - t0:.2f}s + decompress {t2 - t1:.2f}s")
+
+
+def run_reference(args):
+    rank, world = _rank_world()
+    if rank != 0:
+        return
+    import numpy as np
+    import torch
+    from paper_1703_02438_gb300 import synth
+    side = 256       # bounded sample of the same workload: a 256^3 sub-volume recipe
+    series = synth.flash_series(side=side, steps=3, device="cpu")
+    p, x = series[1], series[2]
+    times = []
+    for i in range(args.warmup + args.steps):
+        gbs, sec, desc = cpu_oracle_sample((p, x), args.cpu_sample)
+        if i >= args.warmup:
+            times.append(sec)
+    n = min(args.cpu_sample, p.numel())
+    value = n * 8 / statistics.mean(times) / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world = _rank_world()
+    import numpy as np
+    import torch
+    from paper_1703_02438_gb300 import build as nbuild
+    from paper_1703_02438_gb300 import numarck as N
+    from paper_1703_02438_gb300 import synth
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = _init_dist(world)
+    if rank == 0:
+        nbuild.build()
+    _barrier(dist)
+    nbuild.build()
+    N.lib()
+    dev = torch.device("cuda", local)
+    side = args.side
+    n = side ** 3
+    xs = synth.flash_series(side=side, steps=4, device=dev, seed=synth.seed_for(1, rank))
+    torch.cuda.synchronize()
+    params = {(E, B): N.make_params(torch.float64, B, E) for E, B in COMBOS}
+    bound = max(N.compress_bound(n, p) for p in params.values())
+    blob = torch.empty(bound, dtype=torch.uint8, device=dev)
+    recon = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(2)]
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = N.Workspace(dev)
+    ws.get(max(N.workspace_bytes(n, p) for p in params.values()))
+    stream = torch.cuda.current_stream()
+
+    n_pairs = len(COMBOS) * 3
+    ev_pool = []
+
+    def new_events(k):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        for e in evs:          # torch creates the CUDA event on first record
+            e.record(stream)
+        ev_pool.append(evs)
+        return evs
+
+    def step(trace: bool):
+        for E, B in COMBOS:
+            prev = xs[0]
+            for t in range(1, 4):
+                if trace:
+                    N.trace_events(new_events(4))
+                N.compress(prev, xs[t], E, B, blob=blob, workspace=ws)
+                if trace:
+                    N.trace_events(new_events(2))
+                out = recon[t % 2]
+                N.decompress(blob, prev, out=out, status=status)
+                prev = out
+        if trace:
+            N.trace_events(None)
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    if int(status.item()) != 0:
+        raise RuntimeError(f"device status {int(status.item())} after warm-up")
+
+    clocks = Clocks(local)
+    _barrier(dist)
+    torch.cuda.synchronize()
+    ev_pool.clear()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        step(True)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    _barrier(dist)
+    clk = clocks.stop()
+    ms_total = t_start.elapsed_time(t_end)
+    ms_total = _max_over_ranks(dist, ms_total)
+    ms_step = ms_total / args.steps
+    bytes_rank = args.steps * n_pairs * n * 8
+    value = _sum_over_ranks(dist, bytes_rank) / (ms_total / 1e3) / 1e9
+
+    # per-kernel times from the trace events (compress: K1, K2, K3; decompress: K4)
+    k1 = k2 = k3 = k4 = 0.0
+    nc = nd = 0
+    for evs in ev_pool:
+        if len(evs) == 4:
+            k1 += evs[0].elapsed_time(evs[1])
+            k2 += evs[1].elapsed_time(evs[2])
+            k3 += evs[2].elapsed_time(evs[3])
+            nc += 1
+        else:
+            k4 += evs[0].elapsed_time(evs[1])
+            nd += 1
+    # algorithmic bytes per launch (HBM roofline); n_inc / B from the last blob of each combo
+    hdr = N.parse_header(N.header_bytes(blob))
+    alpha = hdr["n_inc"] / n
+    Bl = hdr["B"]
+    alg = {"k1_hist": 2 * 8 * n,
+           "k3_assign": 2 * 8 * n + n * Bl / 8 + alpha * n * 8,
+           "k4_decode": (1 - alpha) * n * 8 + n * Bl / 8 + alpha * n * 8 + n * 8}
+    avg = {"k1_hist": k1 / nc, "k3_assign": k3 / nc, "k4_decode": k4 / nd}
+    dominant = max(avg, key=avg.get)
+    peak, peak_kind = _peaks()
+    achieved = alg[dominant] / (avg[dominant] / 1e3) / 1e9
+    kernel_ms = {"k1_hist": round(k1 / nc, 4), "k2_topk": round(k2 / nc, 4),
+                 "k3_assign": round(k3 / nc, 4), "k4_decode": round(k4 / nd, 4)}
+    kernel_gbs = {k: round(alg[k] / (avg[k] / 1e3) / 1e9, 1) for k in alg}
+
+    # end to end through the public API with host buffers: every pair copies its current
+    # timestep host->device (pinned), compresses, copies the used blob bytes and the
+    # reconstruction device->host; the first timestep of each chain is copied in as well
+    e2e = None
+    if not args.no_e2e and args.e2e_steps > 0:
+        host_x = [xs[t].cpu().pin_memory() for t in range(4)]
+        host_blob = torch.empty(bound, dtype=torch.uint8).pin_memory()
+        host_rec = torch.empty(n, dtype=torch.float64).pin_memory()
+        dev_x = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(2)]
+        hb = {"h2d": 0, "d2h": 0}
+
+        def e2e_step():
+            for E, B in COMBOS:
+                dev_x[0].copy_(host_x[0], non_blocking=True)
+                hb["h2d"] += n * 8
+                prev = dev_x[0]
+                for t in range(1, 4):
+                    cur = dev_x[1]
+                    cur.copy_(host_x[t], non_blocking=True)
+                    hb["h2d"] += n * 8
+                    N.compress(prev, cur, E, B, blob=blob, workspace=ws)
+                    hbytes = N.header_bytes(blob)          # result size (device -> host)
+                    size = N.blob_size(hbytes)
+                    host_blob[:size].copy_(blob[:size], non_blocking=True)
+                    out = recon[t % 2]
+                    N.decompress(blob, prev, header=hbytes, out=out)
+                    host_rec.copy_(out, non_blocking=True)
+                    hb["d2h"] += size + n * 8
+                    torch.cuda.current_stream().synchronize()
+                    prev = out                             # the chain's prev stays on device
+
+        e2e_step()
+        torch.cuda.synchronize()
+        hb["h2d"] = hb["d2h"] = 0
+        _barrier(dist)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = _max_over_ranks(dist, a.elapsed_time(b))
+        e2e_val = _sum_over_ranks(dist, args.e2e_steps * n_pairs * n * 8) / (e2e_ms / 1e3) / 1e9
+        e2e = {"value": e2e_val, "unit": "GB/s",
+               "h2d_bytes_per_step": hb["h2d"] // args.e2e_steps,
+               "d2h_bytes_per_step": hb["d2h"] // args.e2e_steps,
+               "steps": args.e2e_steps}
+        del host_x, host_blob, host_rec, dev_x
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        gbs, sec, desc = cpu_oracle_sample((xs[1], xs[2]), args.cpu_sample)
+        cpu = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc,
+               "seconds": round(sec, 2)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "pairs_per_step": n_pairs,
+                       "l2": "inputs 8 GiB per array >> 129 MB L2: no flush",
+                       "parallelism": f"replicas x{world} (independent series per GPU)"},
+            "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved,
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": _traffic(dominant, side),
+                         "algorithmic_bytes_per_launch": alg[dominant]},
+            "kernels_ms": kernel_ms, "kernels_gbs": kernel_gbs,
+            "compress_gbs": n * 8 / ((k1 + k2 + k3) / nc / 1e3) / 1e9,
+            "decompress_gbs": n * 8 / (k4 / nd / 1e3) / 1e9,
+            "alpha_last": alpha, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": args.steps * n_pairs * 4,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -84,7 +84,7 @@ typedef struct numarck_params {
   double  E;            /* error bound, 2^-60 <= E < 1; bin width is 2E (§IV.B.1)          */
   int32_t anchor;       /* NUMARCK_ANCHOR_ZERO or NUMARCK_ANCHOR_MIN                      */
   int32_t reserved;     /* must be 0                                                       */
-  int64_t block_bytes;  /* index-table block size in bytes, 16..2^30; 0 = the 1 MB default */
+  int64_t block_bytes;  /* index-table block size in bytes, 2..2^30; 0 = the 1 MB default  */
 } numarck_params;
 
 /*
@@ -214,18 +214,24 @@ int numarck_blob_size(const void* header_host, size_t* bytes);
 int numarck_read_header(const void* header_host, numarck_header* out);
 
 /* ---- decompression (Eq. 4, §III.E) ----
- * blob        : device pointer to a complete blob.
- * header_host : host copy of its header (NUMARCK_HEADER_BYTES), or NULL; with NULL the
- *               call copies the header from the device and synchronises the stream first
- *               (synchronous).
+ * blob        : device pointer to a complete blob (256-byte aligned). The kernel reads the
+ *               header from device memory and checks it (magic, version, status word,
+ *               geometry); a blob produced by numarck_compress on the same stream may be
+ *               decompressed right away, without synchronising.
+ * header_host : optional host copy of its header (NUMARCK_HEADER_BYTES). When given, the
+ *               header and the arguments are validated on the host before any launch and the
+ *               call returns the error code; when NULL, errors found on the device are reported
+ *               only through status_dev.
  * prev        : device array of n elements of T, the same prev the blob was compressed
  *               against.
  * out         : device array of n elements of T; receives the reconstruction. Must not
  *               overlap prev or blob.
  * n           : must equal the header's n.
- * status_dev  : optional device int32; if non-NULL the kernels store a NUMARCK_ERR_* code
- *               into it when the blob's offset tables are inconsistent with its index table
- *               (it is not cleared on success). May be NULL.
+ * status_dev  : optional device int32; if non-NULL the kernel stores a NUMARCK_ERR_* code
+ *               into it when the device header is invalid or its status word is set, when n
+ *               or the range does not match the header, or when the offset tables disagree
+ *               with the index table; nothing is written to out then. It is not cleared on
+ *               success. May be NULL.
  */
 int numarck_decompress(const void* blob, const void* header_host, const void* prev,
                        void* out, int64_t n, int32_t* status_dev, numarck_stream_t stream);
@@ -235,11 +241,22 @@ int numarck_decompress(const void* blob, const void* header_host, const void* pr
  * values of that segment.
  * prev_seg : device array of count elements = prev[start : start+count].
  * out_seg  : device array of count elements; receives R[start : start+count].
- * Returns NUMARCK_ERR_RANGE unless 0 <= start <= start+count <= n.
+ * Returns NUMARCK_ERR_RANGE unless 0 <= start <= start+count <= n (checked on the host when
+ * header_host is given, else on the device through status_dev).
  * The result equals the same slice of numarck_decompress's output, bit for bit. */
 int numarck_decompress_range(const void* blob, const void* header_host,
                              const void* prev_seg, int64_t start, int64_t count,
                              void* out_seg, int32_t* status_dev, numarck_stream_t stream);
+
+/* ---- tracing (kernel-level timing for profilers and benchmarks) ----
+ * events : an array of `count` cudaEvent_t handles owned by the caller, or NULL to stop.
+ * While set, every numarck_compress call made on this host thread records, on its stream,
+ * events[0] before its first kernel and events[1], events[2], events[3] after the ratio +
+ * histogram kernel(s), the top-k kernel and the assign + pack kernel; every
+ * numarck_decompress[_range] call records events[0] before and events[1] after its kernel.
+ * A call needs count >= 4 (compress) or >= 2 (decompress) to record anything.
+ * Returns NUMARCK_ERR_INVALID_ARG if count < 0. */
+int numarck_trace_events(void* const* events, int count);
 
 /* Human-readable name of a status code (static string). */
 const char* numarck_status_string(int code);

@@ -1,0 +1,296 @@
+// capi.cu — the extern "C" boundary of the NUMARCK library (declared in include/numarck.h).
+//
+// Host side only: argument validation, blob geometry (§IV.C block layout, §IV.D arrays),
+// workspace layout, and the launch sequence K0 (ANCHOR_MIN) -> K1 -> K2 -> K3 for compression
+// and K4 for (partial) decompression. Nothing here allocates device memory.
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+
+#include "launch.h"
+
+using namespace nmk;
+
+namespace {
+
+int64_t round_up(int64_t x, int64_t m) { return round_up_i64(x, m); }
+
+// float nearest to v rounded toward -inf / +inf
+float f_down(double v) {
+  float f = (float)v;
+  if ((double)f > v) f = std::nextafter(f, -INFINITY);
+  return f;
+}
+float f_up(double v) {
+  float f = (float)v;
+  if ((double)f < v) f = std::nextafter(f, INFINITY);
+  return f;
+}
+
+int check_params(const numarck_params* p) {
+  if (!p) return NUMARCK_ERR_INVALID_ARG;
+  if (p->dtype != NUMARCK_F32 && p->dtype != NUMARCK_F64) return NUMARCK_ERR_INVALID_ARG;
+  if (p->B < 1 || p->B > NUMARCK_MAX_B) return NUMARCK_ERR_INVALID_ARG;
+  if (!std::isfinite(p->E) || !(p->E >= 0x1p-60) || !(p->E < 1.0)) return NUMARCK_ERR_INVALID_ARG;
+  if (p->anchor != NUMARCK_ANCHOR_ZERO && p->anchor != NUMARCK_ANCHOR_MIN)
+    return NUMARCK_ERR_INVALID_ARG;
+  if (p->reserved != 0) return NUMARCK_ERR_INVALID_ARG;
+  if (p->block_bytes != 0 && (p->block_bytes < 2 || p->block_bytes > ((int64_t)1 << 30)))
+    return NUMARCK_ERR_INVALID_ARG;
+  return NUMARCK_OK;
+}
+
+int64_t effective_block_bytes(const numarck_params* p) {
+  return p->block_bytes ? p->block_bytes : (int64_t)NUMARCK_DEFAULT_BLOCK_BYTES;
+}
+
+WsLayout make_ws(const Geometry& g) {
+  WsLayout w{};
+  size_t o = 0;
+  w.ctrl = o;
+  o += sizeof(Ctrl);
+  w.hist = o;
+  o = (size_t)round_up((int64_t)(o + (size_t)HWIN * 8), 256);
+  w.rank = o;
+  o = (size_t)round_up((int64_t)(o + (size_t)HWIN * 2), 256);
+  w.mtab = o;
+  o += (size_t)65536 * 8;
+  w.cftab = o;
+  o += (size_t)65536 * 4;
+  w.selb = o;
+  o += (size_t)65536 * 4;
+  w.status = o;
+  o = (size_t)round_up((int64_t)(o + (size_t)g.nsub * 8), 256);
+  w.total = o;
+  return w;
+}
+
+template <typename T>
+Consts<T> make_consts(double E, int anchor) {
+  Consts<T> c{};
+  c.E_T = (T)E;
+  c.w = c.E_T + c.E_T;
+  c.inv_w = (T)1 / c.w;
+  c.cap = c.w * (T)(1 << WIN_LOG2);
+  c.a = anchor == NUMARCK_ANCHOR_ZERO ? -c.E_T : (T)0;
+  c.hbase = anchor == NUMARCK_ANCHOR_ZERO ? -((1 << WIN_LOG2) + HMARGIN) : -HMARGIN;
+  c.af = (float)c.a;
+  c.inv_wf = (float)c.inv_w;
+  c.Ef = (float)c.E_T;
+  c.cap_lo = f_down((double)c.cap * (1.0 - 0x1p-19));
+  c.cap_hi = f_up((double)c.cap * (1.0 + 0x1p-19));
+  c.K1 = f_up(0x1p-20 * (double)c.inv_w);
+  c.K0 = f_up(0x1p-22 * (double)c.inv_w * std::fabs((double)c.a) + 0x1p-100);
+  return c;
+}
+
+int device_sms() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (dev < 64 && cache[dev]) return cache[dev];
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+  if (dev < 64) cache[dev] = sms;
+  return sms;
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+thread_local void* const* g_trace = nullptr;
+thread_local int g_trace_count = 0;
+
+void trace(int i, int need, cudaStream_t s) {
+  if (g_trace && g_trace_count >= need && g_trace[i])
+    cudaEventRecord(static_cast<cudaEvent_t>(g_trace[i]), s);
+}
+
+int decode(const void* blob, const void* header_host, const void* prev_seg, int64_t start,
+           int64_t count, void* out_seg, int64_t n_expected, int32_t* status_dev,
+           numarck_stream_t stream) {
+  if (!blob || !aligned(blob, 256)) return NUMARCK_ERR_INVALID_ARG;
+  if (count < 0 || start < 0) return NUMARCK_ERR_RANGE;
+  int64_t ntiles = 0;
+  if (header_host) {
+    numarck_header h;
+    std::memcpy(&h, header_host, sizeof(h));
+    Geometry g;
+    const int rc = check_header(h, &g);
+    if (rc) return rc;
+    if (n_expected >= 0 && n_expected != h.n) return NUMARCK_ERR_INVALID_ARG;
+    if (start > h.n || count > h.n - start) return NUMARCK_ERR_RANGE;
+    if (count == 0) return NUMARCK_OK;
+    const size_t L = h.dtype == NUMARCK_F64 ? 8 : 4;
+    if (!prev_seg || !out_seg || !aligned(prev_seg, L) || !aligned(out_seg, L))
+      return NUMARCK_ERR_INVALID_ARG;
+    const int64_t first = start, last = start + count - 1;
+    const int64_t q0 = first / g.epb, q1 = last / g.epb;
+    ntiles = (q1 * g.spb + (last - q1 * g.epb) / SUB) - (q0 * g.spb + (first - q0 * g.epb) / SUB) + 1;
+  } else {
+    if (count == 0) return NUMARCK_OK;
+    if (!prev_seg || !out_seg || !aligned(prev_seg, 4) || !aligned(out_seg, 4))
+      return NUMARCK_ERR_INVALID_ARG;
+  }
+  DecodePlan P{};
+  P.blob = static_cast<const unsigned char*>(blob);
+  P.prev_seg = prev_seg;
+  P.out_seg = out_seg;
+  P.status = status_dev;
+  P.start = start;
+  P.count = count;
+  P.n_expected = n_expected;
+  P.ntiles_hint = ntiles;
+  P.sms = device_sms();
+  if (P.sms <= 0) return NUMARCK_ERR_CUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  trace(0, 2, s);
+  if (launch_decode(P, s) != cudaSuccess) return NUMARCK_ERR_CUDA;
+  trace(1, 2, s);
+  return NUMARCK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t numarck_compress_bound(int64_t n, const numarck_params* p) {
+  if (check_params(p) || n < 0 || n > MAX_N) return 0;
+  const Geometry g = make_geometry(n, p->dtype, p->B, effective_block_bytes(p), p->anchor);
+  return (size_t)(g.off_exact + n * (p->dtype == NUMARCK_F64 ? 8 : 4));
+}
+
+size_t numarck_workspace_bytes(int64_t n, const numarck_params* p) {
+  if (check_params(p) || n < 0 || n > MAX_N) return 0;
+  const Geometry g = make_geometry(n, p->dtype, p->B, effective_block_bytes(p), p->anchor);
+  return make_ws(g).total;
+}
+
+int numarck_workspace_init(void* ws, size_t ws_bytes, numarck_stream_t stream) {
+  if (!ws) return NUMARCK_ERR_INVALID_ARG;
+  if (cudaMemsetAsync(ws, 0, ws_bytes, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return NUMARCK_ERR_CUDA;
+  return NUMARCK_OK;
+}
+
+int numarck_compress(const void* prev, const void* cur, int64_t n, const numarck_params* p,
+                     void* blob, size_t blob_cap, void* ws, size_t ws_bytes,
+                     numarck_stream_t stream) {
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (n < 0 || n > MAX_N) return NUMARCK_ERR_INVALID_ARG;
+  if (!blob || !ws || !aligned(blob, 256) || !aligned(ws, 256)) return NUMARCK_ERR_INVALID_ARG;
+  const size_t L = p->dtype == NUMARCK_F64 ? 8 : 4;
+  if (n > 0 && (!prev || !cur || !aligned(prev, L) || !aligned(cur, L)))
+    return NUMARCK_ERR_INVALID_ARG;
+  const int64_t bb = effective_block_bytes(p);
+  const Geometry g = make_geometry(n, p->dtype, p->B, bb, p->anchor);
+  const WsLayout wl = make_ws(g);
+  if (blob_cap < (size_t)(g.off_exact + n * (int64_t)L)) return NUMARCK_ERR_CAPACITY;
+  if (ws_bytes < wl.total) return NUMARCK_ERR_CAPACITY;
+
+  CompressPlan P{};
+  P.prev = prev;
+  P.cur = cur;
+  P.blob = static_cast<unsigned char*>(blob);
+  P.ws = static_cast<unsigned char*>(ws);
+  P.wl = wl;
+  P.g = g;
+  P.aligned16 = aligned(prev, 16) && aligned(cur, 16);
+  P.sms = device_sms();
+  if (P.sms <= 0) return NUMARCK_ERR_CUDA;
+  if (p->dtype == NUMARCK_F64)
+    P.cd = make_consts<double>(p->E, p->anchor);
+  else
+    P.cf = make_consts<float>(p->E, p->anchor);
+
+  numarck_header& h = P.hdr;
+  std::memset(&h, 0, sizeof(h));
+  h.magic = NUMARCK_MAGIC;
+  h.version = NUMARCK_VERSION;
+  h.dtype = p->dtype;
+  h.B = p->B;
+  h.E = p->E;
+  h.anchor = p->anchor;
+  h.status = 0;
+  h.n = n;
+  h.block_bytes = bb;
+  h.epb = g.epb;
+  h.nblocks = g.nblocks;
+  h.sub = SUB;
+  h.nsub = g.nsub;
+  h.block_stride = g.block_stride;
+  h.off_centres = g.off_centres;
+  h.off_idx_off = g.off_idx_off;
+  h.off_inc_off = g.off_inc_off;
+  h.off_sub_off = g.off_sub_off;
+  h.off_index = g.off_index;
+  h.off_exact = g.off_exact;
+  h.total_bytes = g.off_exact;
+
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  trace(0, 4, s);
+  if (p->anchor == NUMARCK_ANCHOR_MIN && launch_anchor_min(P, s) != cudaSuccess)
+    return NUMARCK_ERR_CUDA;
+  if (launch_hist(P, s) != cudaSuccess) return NUMARCK_ERR_CUDA;
+  trace(1, 4, s);
+  if (launch_topk(P, s) != cudaSuccess) return NUMARCK_ERR_CUDA;
+  trace(2, 4, s);
+  if (launch_assign(P, s) != cudaSuccess) return NUMARCK_ERR_CUDA;
+  trace(3, 4, s);
+  return NUMARCK_OK;
+}
+
+int numarck_read_header(const void* header_host, numarck_header* out) {
+  if (!header_host) return NUMARCK_ERR_INVALID_ARG;
+  numarck_header h;
+  std::memcpy(&h, header_host, sizeof(h));
+  const int rc = check_header(h, nullptr);
+  if (rc) return rc;
+  if (out) *out = h;
+  return NUMARCK_OK;
+}
+
+int numarck_blob_size(const void* header_host, size_t* bytes) {
+  numarck_header h;
+  const int rc = numarck_read_header(header_host, &h);
+  if (rc) return rc;
+  if (bytes) *bytes = (size_t)h.total_bytes;
+  return NUMARCK_OK;
+}
+
+int numarck_decompress(const void* blob, const void* header_host, const void* prev, void* out,
+                       int64_t n, int32_t* status_dev, numarck_stream_t stream) {
+  if (n < 0) return NUMARCK_ERR_INVALID_ARG;
+  return decode(blob, header_host, prev, 0, n, out, n, status_dev, stream);
+}
+
+int numarck_decompress_range(const void* blob, const void* header_host, const void* prev_seg,
+                             int64_t start, int64_t count, void* out_seg, int32_t* status_dev,
+                             numarck_stream_t stream) {
+  return decode(blob, header_host, prev_seg, start, count, out_seg, -1, status_dev, stream);
+}
+
+int numarck_trace_events(void* const* events, int count) {
+  if (count < 0) return NUMARCK_ERR_INVALID_ARG;
+  g_trace = count ? events : nullptr;
+  g_trace_count = events ? count : 0;
+  return NUMARCK_OK;
+}
+
+const char* numarck_status_string(int code) {
+  switch (code) {
+    case NUMARCK_OK: return "ok";
+    case NUMARCK_ERR_INVALID_ARG: return "invalid argument";
+    case NUMARCK_ERR_CAPACITY: return "buffer too small";
+    case NUMARCK_ERR_CUDA: return "CUDA error";
+    case NUMARCK_ERR_CORRUPT: return "corrupt or inconsistent blob";
+    case NUMARCK_ERR_RANGE: return "range outside [0, n]";
+    case NUMARCK_ERR_TIMEOUT: return "device wait timed out";
+    case NUMARCK_ERR_NOMEM: return "out of host memory";
+    default: return "unknown status";
+  }
+}
+
+const char* numarck_version(void) { return "numarck-gb300 1 sm_103a"; }
+
+}  // extern "C"

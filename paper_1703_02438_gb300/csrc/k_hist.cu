@@ -1,0 +1,297 @@
+// k_hist.cu — K0: minimum binnable ratio (ANCHOR_MIN grid origin, §IV.A computes the global
+// min/max of the change ratios); K1: change ratio (Eq. 1) -> bin id -> top-k histogram
+// (§IV.B.1), fused in one pass over both timesteps with 128-bit streaming loads.
+//
+// The paper builds a local histogram per MPI rank and merges them with MPI_Allreduce (§IV.B.1).
+// Here each CTA keeps a private shared-memory histogram over a 16384-bin window around the
+// zero-change bin; lanes of a warp that hit the same bin are merged with match.any before one
+// shared atomic, and each CTA merges its window into the global histogram once at the end.
+// Bins outside the shared window go straight to the global window with one atomic.
+#include "launch.h"
+
+namespace nmk {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ void anchor_min_consts(Consts<T>& c, const Ctrl* ctrl) {
+  const unsigned long long key = ctrl->amin_key;
+  double a = key ? key_to_ratio(key) : 0.0;
+  if (a == 0.0) a = 0.0;  // a zero minimum is taken as +0
+  c.a = (T)a;             // exact: the key was made from a T value
+  c.af = (float)c.a;
+  c.K0 = __fadd_ru(__fmul_ru(__fmul_ru(0x1p-22f, c.inv_wf), fabsf(c.af)), 0x1p-100f);
+}
+
+// ---------------------------------------------------------------------------------------
+// K0: per-element exact ratio, binnable test, max of the order key (= min ratio)
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(512) k0_anchor_min(const T* __restrict__ prev,
+                                                     const T* __restrict__ cur, int64_t n,
+                                                     Consts<T> c, Ctrl* ctrl) {
+  unsigned long long best = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+    const T p = ld_stream(prev + j), x = ld_stream(cur + j);
+    const T d = t_sub(x, p);
+    const T r = t_div(d, p);
+    if (t_abs(r) <= c.cap) {
+      const unsigned long long k = min_key(r);
+      best = k > best ? k : best;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, best, o);
+    best = t > best ? t : best;
+  }
+  if (lane_id() == 0 && best) atomicMax(&ctrl->amin_key, best);
+}
+
+// ---------------------------------------------------------------------------------------
+// K1
+// ---------------------------------------------------------------------------------------
+struct HistCtx {
+  unsigned int* sh;
+  unsigned long long* hist;
+  Ctrl* ctrl;
+  int sbase;
+  int hbase;
+};
+
+// All 32 lanes call this together (valid may differ per lane).
+__device__ __forceinline__ void hist_add(const HistCtx& h, bool valid, int b) {
+  const unsigned key = valid ? (unsigned)b : 0x80000000u;   // INT_MIN is never a bin
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  if (valid && (int)lane_id() == __ffs(peers) - 1) {
+    const unsigned cnt = __popc(peers);
+    const int si = b - h.sbase;
+    if ((unsigned)si < (unsigned)SH_BINS) {
+      atomicAdd(&h.sh[si], cnt);
+    } else {
+      const int gi = b - h.hbase;
+      if ((unsigned)gi < (unsigned)HWIN)
+        atomicAdd(&h.hist[gi], (unsigned long long)cnt);
+      else
+        atomicOr(&h.ctrl->win_err, 1u);
+    }
+  }
+}
+
+template <typename T>
+struct Classifier;
+
+template <>
+struct Classifier<float> {
+  __device__ __forceinline__ static int run(float p, float x, const Consts<float>& c, int& b) {
+    return classify_exact<float>(p, x, c, b);
+  }
+};
+template <>
+struct Classifier<double> {
+  __device__ __forceinline__ static int run(double p, double x, const Consts<double>& c, int& b) {
+    Est e;
+    return classify_f64(p, x, c, b, e);
+  }
+};
+
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+  using type = float4;
+  static constexpr int N = 4;
+  __device__ __forceinline__ static void get(const type& v, float* o) {
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+};
+template <>
+struct Vec<double> {
+  using type = double2;
+  static constexpr int N = 2;
+  __device__ __forceinline__ static void get(const type& v, double* o) {
+    o[0] = v.x; o[1] = v.y;
+  }
+};
+
+constexpr int K1_THREADS = 512;
+constexpr int K1_UNROLL = 4;
+
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(K1_THREADS) k1_hist(const T* __restrict__ prev,
+                                                      const T* __restrict__ cur, int64_t n,
+                                                      Consts<T> c, int anchor_min, Ctrl* ctrl,
+                                                      unsigned long long* hist,
+                                                      unsigned long long* tstatus, int64_t nsub) {
+  extern __shared__ unsigned int sh[];
+  if (anchor_min) anchor_min_consts<T>(c, ctrl);
+  int c0 = 0;  // bin of a zero change ratio: centre of the shared window
+  if (anchor_min) {
+    const double z = floor(-(double)c.a * (double)c.inv_w);
+    c0 = (int)fmin(fmax(z, 0.0), (double)(1 << (WIN_LOG2 + 1)));
+  }
+  HistCtx h{sh, hist, ctrl, c0 - SH_BINS / 2, c.hbase};
+
+  for (int i = threadIdx.x; i < SH_BINS; i += blockDim.x) sh[i] = 0u;
+  // K3's scan state and tile counter for this call
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->ticket = 0u;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nsub;
+       i += (int64_t)gridDim.x * blockDim.x)
+    tstatus[i] = 0ull;
+  __syncthreads();
+
+  int lmin = 0x7FFFFFFF, lmax = (int)0x80000000;
+  const int lane = (int)lane_id();
+  const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+
+  if (VEC) {
+    using V = Vec<T>;
+    using VT = typename V::type;
+    const VT* pv = reinterpret_cast<const VT*>(prev);
+    const VT* xv = reinterpret_cast<const VT*>(cur);
+    const int64_t nvec = n / V::N;
+    for (int64_t base = gwarp * (32 * K1_UNROLL); base < nvec; base += nwarps * (32 * K1_UNROLL)) {
+      T pe[K1_UNROLL][V::N], xe[K1_UNROLL][V::N];
+      bool ok[K1_UNROLL];
+#pragma unroll
+      for (int u = 0; u < K1_UNROLL; ++u) {
+        const int64_t vi = base + u * 32 + lane;
+        ok[u] = vi < nvec;
+        VT a = {}, b = {};
+        if (ok[u]) { a = __ldcs(pv + vi); b = __ldcs(xv + vi); }
+        V::get(a, pe[u]);
+        V::get(b, xe[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < K1_UNROLL; ++u) {
+#pragma unroll
+        for (int v = 0; v < V::N; ++v) {
+          int b = 0;
+          const bool binned = ok[u] && Classifier<T>::run(pe[u][v], xe[u][v], c, b);
+          if (binned) { lmin = min(lmin, b); lmax = max(lmax, b); }
+          hist_add(h, binned, b);
+        }
+      }
+    }
+    // scalar tail (< V elements), one warp
+    const int64_t t0 = nvec * V::N;
+    if (t0 < n && gwarp == 0) {
+      const int64_t j = t0 + lane;
+      int b = 0;
+      bool binned = false;
+      if (j < n) binned = Classifier<T>::run(ld_stream(prev + j), ld_stream(cur + j), c, b);
+      if (binned) { lmin = min(lmin, b); lmax = max(lmax, b); }
+      hist_add(h, binned, b);
+    }
+  } else {
+    constexpr int U = 8;
+    for (int64_t base = gwarp * (32 * U); base < n; base += nwarps * (32 * U)) {
+      T pe[U], xe[U];
+      bool ok[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t j = base + u * 32 + lane;
+        ok[u] = j < n;
+        pe[u] = ok[u] ? ld_stream(prev + j) : (T)0;
+        xe[u] = ok[u] ? ld_stream(cur + j) : (T)0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        int b = 0;
+        const bool binned = ok[u] && Classifier<T>::run(pe[u], xe[u], c, b);
+        if (binned) { lmin = min(lmin, b); lmax = max(lmax, b); }
+        hist_add(h, binned, b);
+      }
+    }
+  }
+
+  // bin range of this CTA -> one atomic per CTA on each key
+  __shared__ int s_min, s_max;
+  if (threadIdx.x == 0) { s_min = 0x7FFFFFFF; s_max = (int)0x80000000; }
+  __syncthreads();
+  lmin = __reduce_min_sync(0xffffffffu, lmin);
+  lmax = __reduce_max_sync(0xffffffffu, lmax);
+  if (lane == 0 && lmin <= lmax) { atomicMin(&s_min, lmin); atomicMax(&s_max, lmax); }
+  __syncthreads();
+  if (threadIdx.x == 0 && s_min <= s_max) {
+    atomicMax(&ctrl->bmin_key, KEY_BIAS - (unsigned)s_min);
+    atomicMax(&ctrl->bmax_key, (unsigned)s_max + KEY_BIAS);
+  }
+  // merge the shared window into the global histogram
+  for (int i = threadIdx.x; i < SH_BINS; i += blockDim.x) {
+    const unsigned v = sh[i];
+    if (v) {
+      const int gi = h.sbase + i - h.hbase;
+      if ((unsigned)gi < (unsigned)HWIN)
+        atomicAdd(&hist[gi], (unsigned long long)v);
+      else
+        atomicOr(&ctrl->win_err, 1u);
+    }
+  }
+}
+
+template <typename T>
+const Consts<T>& consts_of(const CompressPlan& P);
+template <>
+const Consts<float>& consts_of<float>(const CompressPlan& P) { return P.cf; }
+template <>
+const Consts<double>& consts_of<double>(const CompressPlan& P) { return P.cd; }
+
+int grid_for(int64_t work_items, int per_block_items, int max_blocks) {
+  int64_t b = (work_items + per_block_items - 1) / per_block_items;
+  if (b < 1) b = 1;
+  if (b > max_blocks) b = max_blocks;
+  return (int)b;
+}
+
+template <typename T>
+cudaError_t launch_anchor_min_t(const CompressPlan& P, cudaStream_t s) {
+  Ctrl* ctrl = reinterpret_cast<Ctrl*>(P.ws + P.wl.ctrl);
+  const int blocks = grid_for(P.g.n, 512 * 8, P.sms * 4);
+  k0_anchor_min<T><<<blocks, 512, 0, s>>>(static_cast<const T*>(P.prev),
+                                          static_cast<const T*>(P.cur), P.g.n, consts_of<T>(P),
+                                          ctrl);
+  return cudaGetLastError();
+}
+
+template <typename T, bool VEC>
+cudaError_t launch_hist_tv(const CompressPlan& P, cudaStream_t s) {
+  static thread_local int configured_dev = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const size_t smem = SH_BINS * sizeof(unsigned int);
+  if (configured_dev != dev) {
+    cudaError_t e = cudaFuncSetAttribute(k1_hist<T, VEC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured_dev = dev;
+  }
+  Ctrl* ctrl = reinterpret_cast<Ctrl*>(P.ws + P.wl.ctrl);
+  auto* hist = reinterpret_cast<unsigned long long*>(P.ws + P.wl.hist);
+  auto* tstat = reinterpret_cast<unsigned long long*>(P.ws + P.wl.status);
+  // 3 CTAs of 512 threads per SM (64 KB shared window each); enough elements per CTA that the
+  // window set-up and merge stay small next to the streaming work.
+  const int blocks = grid_for(P.g.n, K1_THREADS * 32, P.sms * 3);
+  k1_hist<T, VEC><<<blocks, K1_THREADS, smem, s>>>(
+      static_cast<const T*>(P.prev), static_cast<const T*>(P.cur), P.g.n, consts_of<T>(P),
+      P.g.anchor == NUMARCK_ANCHOR_MIN ? 1 : 0, ctrl, hist, tstat, P.g.nsub);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_anchor_min(const CompressPlan& P, cudaStream_t s) {
+  if (P.g.n == 0) return cudaSuccess;
+  return P.g.dtype == NUMARCK_F64 ? launch_anchor_min_t<double>(P, s)
+                                  : launch_anchor_min_t<float>(P, s);
+}
+
+cudaError_t launch_hist(const CompressPlan& P, cudaStream_t s) {
+  if (P.g.dtype == NUMARCK_F64)
+    return P.aligned16 ? launch_hist_tv<double, true>(P, s) : launch_hist_tv<double, false>(P, s);
+  return P.aligned16 ? launch_hist_tv<float, true>(P, s) : launch_hist_tv<float, false>(P, s);
+}
+
+}  // namespace nmk

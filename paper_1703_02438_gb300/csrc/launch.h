@@ -1,0 +1,42 @@
+// launch.h — host-side launchers of the NUMARCK kernels (one translation unit per kernel family).
+#pragma once
+
+#include "common.cuh"
+
+namespace nmk {
+
+// Everything a compression launch needs; built and validated by the C ABI (capi.cu).
+struct CompressPlan {
+  const void* prev;
+  const void* cur;
+  unsigned char* blob;
+  unsigned char* ws;
+  WsLayout wl;
+  Geometry g;
+  numarck_header hdr;      // header as known before the kernels run (n_sel, a, n_inc patched)
+  Consts<float> cf;        // valid when dtype == F32
+  Consts<double> cd;       // valid when dtype == F64
+  bool aligned16;          // prev and cur both 16-byte aligned
+  int sms;                 // multiprocessors of the current device
+};
+
+// Decompression of elements [start, start+count). The kernel takes the blob's geometry from the
+// header in device memory and validates it there; n_expected >= 0 must equal the header's n.
+// ntiles_hint > 0 (known when the caller supplied a host copy of the header) sizes the grid.
+struct DecodePlan {
+  const unsigned char* blob;
+  const void* prev_seg;
+  void* out_seg;
+  int32_t* status;
+  int64_t start, count, n_expected;
+  int64_t ntiles_hint;
+  int sms;
+};
+
+cudaError_t launch_anchor_min(const CompressPlan& P, cudaStream_t s);  // K0 (ANCHOR_MIN only)
+cudaError_t launch_hist(const CompressPlan& P, cudaStream_t s);        // K1
+cudaError_t launch_topk(const CompressPlan& P, cudaStream_t s);        // K2
+cudaError_t launch_assign(const CompressPlan& P, cudaStream_t s);      // K3
+cudaError_t launch_decode(const DecodePlan& P, cudaStream_t s);        // K4 / K5
+
+}  // namespace nmk

@@ -1,0 +1,235 @@
+"""Thin Python binding of libnumarck.so (the C ABI of include/numarck.h).
+
+Argument marshalling only: every step of compression and decompression runs in the library's
+CUDA kernels. torch supplies device memory and the current CUDA stream. If the library has not
+been built, every call raises; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import struct
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libnumarck.so")
+
+OK = 0
+ERR_INVALID_ARG = 1
+ERR_CAPACITY = 2
+ERR_CUDA = 3
+ERR_CORRUPT = 4
+ERR_RANGE = 5
+ERR_TIMEOUT = 6
+ERR_NOMEM = 7
+F32 = 0
+F64 = 1
+ANCHOR_ZERO = 0
+ANCHOR_MIN = 1
+HEADER_BYTES = 256
+
+HEADER_FIELDS = ("magic", "version", "dtype", "B", "E", "anchor", "status", "n", "block_bytes",
+                 "epb", "nblocks", "sub", "nsub", "n_sel", "n_inc", "a", "block_stride",
+                 "off_centres", "off_idx_off", "off_inc_off", "off_sub_off", "off_index",
+                 "off_exact", "total_bytes")
+_HEADER_FMT = "<IIiidiiqqqqqqqqdqqqqqqqq"
+
+
+class NumarckError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {status_string(code)} (status {code})")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("B", ctypes.c_int32), ("E", ctypes.c_double),
+                ("anchor", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("block_bytes", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t
+        pp = ctypes.POINTER(Params)
+        L.numarck_compress_bound.argtypes = [i64, pp]
+        L.numarck_compress_bound.restype = sz
+        L.numarck_workspace_bytes.argtypes = [i64, pp]
+        L.numarck_workspace_bytes.restype = sz
+        L.numarck_workspace_init.argtypes = [vp, sz, vp]
+        L.numarck_workspace_init.restype = i32
+        L.numarck_compress.argtypes = [vp, vp, i64, pp, vp, sz, vp, sz, vp]
+        L.numarck_compress.restype = i32
+        L.numarck_blob_size.argtypes = [vp, ctypes.POINTER(sz)]
+        L.numarck_blob_size.restype = i32
+        L.numarck_read_header.argtypes = [vp, vp]
+        L.numarck_read_header.restype = i32
+        L.numarck_decompress.argtypes = [vp, vp, vp, vp, i64, vp, vp]
+        L.numarck_decompress.restype = i32
+        L.numarck_decompress_range.argtypes = [vp, vp, vp, i64, i64, vp, vp, vp]
+        L.numarck_decompress_range.restype = i32
+        L.numarck_status_string.argtypes = [i32]
+        L.numarck_status_string.restype = ctypes.c_char_p
+        L.numarck_trace_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), i32]
+        L.numarck_trace_events.restype = i32
+        L.numarck_version.argtypes = []
+        L.numarck_version.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return lib().numarck_status_string(int(code)).decode()
+
+
+def _check(code: int, what: str):
+    if code != OK:
+        raise NumarckError(code, what)
+
+
+def make_params(dtype, B: int, E: float, anchor: int = ANCHOR_ZERO, block_bytes: int = 0) -> Params:
+    code = {torch.float32: F32, torch.float64: F64}.get(dtype, dtype)
+    return Params(int(code), int(B), float(E), int(anchor), 0, int(block_bytes))
+
+
+def compress_bound(n: int, params: Params) -> int:
+    return int(lib().numarck_compress_bound(int(n), ctypes.byref(params)))
+
+
+def workspace_bytes(n: int, params: Params) -> int:
+    return int(lib().numarck_workspace_bytes(int(n), ctypes.byref(params)))
+
+
+def _stream_ptr(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Workspace:
+    """A device workspace, zero-filled once and reused (grows on demand)."""
+
+    def __init__(self, device=None):
+        self.device = torch.device(device or "cuda")
+        self.buf = None
+
+    def get(self, nbytes: int, stream=None) -> torch.Tensor:
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            _check(lib().numarck_workspace_init(ctypes.c_void_p(self.buf.data_ptr()), nbytes,
+                                                ctypes.c_void_p(_stream_ptr(stream))),
+                   "numarck_workspace_init")
+        return self.buf
+
+
+_default_ws = {}
+
+
+def _workspace_for(device) -> Workspace:
+    key = torch.device(device).index
+    if key not in _default_ws:
+        _default_ws[key] = Workspace(device)
+    return _default_ws[key]
+
+
+def compress(prev: torch.Tensor, cur: torch.Tensor, E: float, B: int, anchor: int = ANCHOR_ZERO,
+             block_bytes: int = 0, blob: torch.Tensor | None = None,
+             workspace: Workspace | None = None, stream=None) -> torch.Tensor:
+    """Queues compression of `cur` against `prev` (1-D CUDA tensors of equal dtype/length).
+
+    Returns the blob buffer (uint8, compress_bound bytes); its header says how many bytes are
+    used (see header()/blob_size())."""
+    if prev.dtype != cur.dtype or prev.shape != cur.shape or prev.dim() != 1:
+        raise ValueError("prev and cur must be 1-D tensors of the same dtype and length")
+    if not (prev.is_cuda and cur.is_cuda):
+        raise ValueError("prev and cur must be CUDA tensors")
+    prev = prev.contiguous()
+    cur = cur.contiguous()
+    params = make_params(prev.dtype, B, E, anchor, block_bytes)
+    n = prev.numel()
+    bound = compress_bound(n, params)
+    if bound == 0:
+        raise NumarckError(ERR_INVALID_ARG, "numarck_compress_bound")
+    if blob is None:
+        blob = torch.empty(bound, dtype=torch.uint8, device=prev.device)
+    ws = (workspace or _workspace_for(prev.device)).get(workspace_bytes(n, params), stream)
+    _check(lib().numarck_compress(ctypes.c_void_p(prev.data_ptr()), ctypes.c_void_p(cur.data_ptr()),
+                                  n, ctypes.byref(params), ctypes.c_void_p(blob.data_ptr()),
+                                  blob.numel(), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                  ctypes.c_void_p(_stream_ptr(stream))), "numarck_compress")
+    return blob
+
+
+def header_bytes(blob: torch.Tensor) -> bytes:
+    """Host copy of the blob header (synchronises with the current stream)."""
+    return bytes(blob[:HEADER_BYTES].cpu().numpy().tobytes())
+
+
+def parse_header(hb: bytes) -> dict:
+    size = struct.calcsize(_HEADER_FMT)
+    return dict(zip(HEADER_FIELDS, struct.unpack(_HEADER_FMT, hb[:size])))
+
+
+def blob_size(hb: bytes) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().numarck_blob_size(ctypes.c_char_p(hb), ctypes.byref(out)), "numarck_blob_size")
+    return int(out.value)
+
+
+def decompress(blob: torch.Tensor, prev: torch.Tensor, header: bytes | None = None,
+               out: torch.Tensor | None = None, status: torch.Tensor | None = None,
+               stream=None) -> torch.Tensor:
+    prev = prev.contiguous()
+    if out is None:
+        out = torch.empty_like(prev)
+    hp = ctypes.c_char_p(header) if header is not None else None
+    sp = ctypes.c_void_p(status.data_ptr()) if status is not None else None
+    _check(lib().numarck_decompress(ctypes.c_void_p(blob.data_ptr()), hp,
+                                    ctypes.c_void_p(prev.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                    prev.numel(), sp, ctypes.c_void_p(_stream_ptr(stream))),
+           "numarck_decompress")
+    return out
+
+
+def decompress_range(blob: torch.Tensor, prev_seg: torch.Tensor, start: int, count: int,
+                     header: bytes | None = None, out: torch.Tensor | None = None,
+                     status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    prev_seg = prev_seg.contiguous()
+    if out is None:
+        out = torch.empty_like(prev_seg)
+    hp = ctypes.c_char_p(header) if header is not None else None
+    sp = ctypes.c_void_p(status.data_ptr()) if status is not None else None
+    _check(lib().numarck_decompress_range(ctypes.c_void_p(blob.data_ptr()), hp,
+                                          ctypes.c_void_p(prev_seg.data_ptr()), int(start),
+                                          int(count), ctypes.c_void_p(out.data_ptr()), sp,
+                                          ctypes.c_void_p(_stream_ptr(stream))),
+           "numarck_decompress_range")
+    return out
+
+
+_trace_keep = None
+
+
+def trace_events(events) -> None:
+    """Record these torch.cuda.Event objects at the kernel boundaries of the following calls on
+    this thread (see numarck_trace_events); None stops recording."""
+    global _trace_keep
+    if events is None:
+        _trace_keep = None
+        _check(lib().numarck_trace_events(None, 0), "numarck_trace_events")
+        return
+    arr = (ctypes.c_void_p * len(events))(*[ctypes.c_void_p(e.cuda_event) for e in events])
+    _trace_keep = arr
+    _check(lib().numarck_trace_events(arr, len(events)), "numarck_trace_events")
+
+
+def version() -> str:
+    return lib().numarck_version().decode()

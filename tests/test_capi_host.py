@@ -1,0 +1,133 @@
+"""Host-side checks of the C ABI (no GPU): the library loads and exports every function that
+include/numarck.h declares; sizing and validation paths agree with the documented format
+(restated by the oracle's layout) and reject bad arguments before touching any device memory."""
+import ctypes
+import os
+import re
+import struct
+
+import numpy as np
+import pytest
+
+from oracle import numarck_oracle as O
+from paper_1703_02438_gb300 import build as B_
+from paper_1703_02438_gb300 import numarck as N
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B_.build()
+    return N.lib()
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "numarck.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(numarck_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared_functions()
+    assert "numarck_compress" in names and "numarck_decompress_range" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_version_and_status_strings(lib):
+    assert "sm_103a" in N.version()
+    for code in range(8):
+        assert N.status_string(code)
+    assert N.status_string(99) == "unknown status"
+
+
+@pytest.mark.parametrize("dtype,T", [(N.F32, np.float32), (N.F64, np.float64)])
+@pytest.mark.parametrize("B", [1, 6, 8, 10, 13, 16])
+@pytest.mark.parametrize("n", [0, 1, 4095, 4096, 4097, 1 << 20, 3758400])
+def test_compress_bound_matches_format(lib, dtype, T, B, n):
+    for bb in (0, 2, 16, 1000, 1 << 20):
+        p = N.Params(dtype, B, 1e-3, 0, 0, bb)
+        want = O.compress_bound(n, T, B, bb or O.DEFAULT_BLOCK_BYTES)
+        assert N.compress_bound(n, p) == want
+        assert N.workspace_bytes(n, p) > (1 << 22) * 8
+
+
+def test_invalid_params_rejected(lib):
+    bad = [N.Params(2, 8, 1e-3, 0, 0, 0), N.Params(0, 0, 1e-3, 0, 0, 0),
+           N.Params(0, 17, 1e-3, 0, 0, 0), N.Params(0, 8, 0.0, 0, 0, 0),
+           N.Params(0, 8, 1.0, 0, 0, 0), N.Params(0, 8, float("nan"), 0, 0, 0),
+           N.Params(0, 8, 2.0 ** -61, 0, 0, 0), N.Params(0, 8, 1e-3, 2, 0, 0),
+           N.Params(0, 8, 1e-3, 0, 1, 0), N.Params(0, 8, 1e-3, 0, 0, 1),
+           N.Params(0, 8, 1e-3, 0, 0, (1 << 30) + 1)]
+    for p in bad:
+        assert N.compress_bound(10, p) == 0
+        assert N.workspace_bytes(10, p) == 0
+    good = N.Params(0, 8, 1e-3, 0, 0, 0)
+    assert N.compress_bound(-1, good) == 0 and N.compress_bound((1 << 40) + 1, good) == 0
+
+
+def test_compress_argument_errors_before_device(lib):
+    """Every case returns before any CUDA call (fake device addresses are never touched)."""
+    p = N.Params(N.F64, 8, 1e-3, 0, 0, 0)
+    n = 1000
+    bound, wsb = N.compress_bound(n, p), N.workspace_bytes(n, p)
+    A = 1 << 20   # a 256-aligned fake address
+    C = lambda prev, cur, n, blob, cap, ws, wsz, pp=p: lib.numarck_compress(
+        ctypes.c_void_p(prev), ctypes.c_void_p(cur), n, ctypes.byref(pp), ctypes.c_void_p(blob),
+        cap, ctypes.c_void_p(ws), wsz, None)
+    assert C(A, A, n, 0, bound, A, wsb) == N.ERR_INVALID_ARG          # null blob
+    assert C(A, A, n, A, bound, 0, wsb) == N.ERR_INVALID_ARG          # null workspace
+    assert C(0, A, n, A, bound, A, wsb) == N.ERR_INVALID_ARG          # null prev
+    assert C(A, A, -5, A, bound, A, wsb) == N.ERR_INVALID_ARG         # negative n
+    assert C(A + 4, A, n, A, bound, A, wsb) == N.ERR_INVALID_ARG      # prev not 8-aligned
+    assert C(A, A, n, A + 16, bound, A, wsb) == N.ERR_INVALID_ARG     # blob not 256-aligned
+    assert C(A, A, n, A, bound - 1, A, wsb) == N.ERR_CAPACITY
+    assert C(A, A, n, A, bound, A, wsb - 1) == N.ERR_CAPACITY
+    bad = N.Params(N.F64, 8, 1e-3, 5, 0, 0)
+    assert C(A, A, n, A, bound, A, wsb, bad) == N.ERR_INVALID_ARG
+
+
+def _oracle_header(n=5000, T=np.float64, B=8, bb=1 << 20):
+    rng = np.random.default_rng(3)
+    p = rng.lognormal(size=n).astype(T)
+    x = (p * (1 + rng.normal(0, 0.01, n))).astype(T)
+    return O.compress(p, x, 1e-3, B, block_bytes=bb).to_bytes()
+
+
+def test_blob_size_and_header_validation(lib):
+    for T, B, bb in ((np.float64, 8, 1 << 20), (np.float32, 13, 100), (np.float64, 3, 17)):
+        data = _oracle_header(T=T, B=B, bb=bb)
+        hb = data[:256]
+        assert N.blob_size(hb) == len(data)
+        hdr = N.parse_header(hb)
+        assert hdr["total_bytes"] == len(data)
+    data = bytearray(_oracle_header())
+    for off, val in ((0, 0xDEAD), (4, 2), (12, 40), (48, 7)):       # magic, version, B, epb
+        bad = bytearray(data[:256])
+        bad[off:off + 4] = struct.pack("<I", val)
+        with pytest.raises(N.NumarckError) as e:
+            N.blob_size(bytes(bad))
+        assert e.value.code == N.ERR_CORRUPT
+    st = bytearray(data[:256])
+    st[28:32] = struct.pack("<i", N.ERR_TIMEOUT)                       # device status word
+    with pytest.raises(N.NumarckError) as e:
+        N.blob_size(bytes(st))
+    assert e.value.code == N.ERR_TIMEOUT
+
+
+def test_decompress_argument_errors_before_device(lib):
+    data = _oracle_header(n=5000)
+    hb = ctypes.c_char_p(data[:256])
+    A = 1 << 20
+    D = lambda start, count: lib.numarck_decompress_range(
+        ctypes.c_void_p(A), hb, ctypes.c_void_p(A), start, count, ctypes.c_void_p(A), None, None)
+    assert D(-1, 10) == N.ERR_RANGE
+    assert D(0, 5001) == N.ERR_RANGE
+    assert D(4990, 11) == N.ERR_RANGE
+    assert D(5000, 0) == N.OK                 # empty segment: nothing to launch
+    full = lambda n: lib.numarck_decompress(ctypes.c_void_p(A), hb, ctypes.c_void_p(A),
+                                            ctypes.c_void_p(A), n, None, None)
+    assert full(4999) == N.ERR_INVALID_ARG    # n must match the header
+    assert lib.numarck_decompress(ctypes.c_void_p(A + 8), hb, ctypes.c_void_p(A),
+                                  ctypes.c_void_p(A), 5000, None, None) == N.ERR_INVALID_ARG

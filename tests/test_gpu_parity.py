@@ -1,0 +1,239 @@
+"""GPU parity: the CUDA path against the CPU oracle, through the C ABI.
+
+Floating point decides only integers and bit copies here (bin ids, indices, packed bits,
+incompressible values), and the reconstruction is one T multiply, so the bar is bit-exact:
+the whole blob (header, centre table, offset tables, index blocks, incompressible table) must be
+byte-identical to the oracle's, and decompression bit-identical. Inputs are the seeded synthetic
+workloads (scaled and full size) plus adversarial cases.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import numarck_oracle as O
+from paper_1703_02438_gb300 import numarck as N
+from paper_1703_02438_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1703_02438_gb300 import build
+    build.build()
+    N.lib()
+
+
+def _u(a: np.ndarray) -> np.ndarray:
+    return a.view(np.uint64 if a.dtype == np.float64 else np.uint32)
+
+
+def _first_diff(a: bytes, b: bytes) -> str:
+    n = min(len(a), len(b))
+    i = next((k for k in range(n) if a[k] != b[k]), n)
+    return f"len {len(a)} vs {len(b)}, first difference at byte {i}"
+
+
+def gpu_compress(prev, cur, E, B, anchor=0, block_bytes=0):
+    blob = N.compress(prev, cur, E, B, anchor=anchor, block_bytes=block_bytes)
+    torch.cuda.synchronize()
+    hb = N.header_bytes(blob)
+    size = N.blob_size(hb)
+    return blob, hb, blob[:size].cpu().numpy().tobytes()
+
+
+def check_pair(p_np, x_np, E, B, anchor=0, block_bytes=0, ranges=(), p_dev=None, x_dev=None):
+    """Compress on the GPU and with the oracle; compare blob bytes, decompression and ranges."""
+    want = O.compress(p_np, x_np, E, B, anchor=anchor,
+                      block_bytes=block_bytes or O.DEFAULT_BLOCK_BYTES).to_bytes()
+    p_dev = torch.from_numpy(p_np).to(DEV) if p_dev is None else p_dev
+    x_dev = torch.from_numpy(x_np).to(DEV) if x_dev is None else x_dev
+    blob, hb, got = gpu_compress(p_dev, x_dev, E, B, anchor, block_bytes)
+    if got != want:
+        hg, hw = O.parse_header(got), O.parse_header(want)
+        diff = {k: (hg[k], hw[k]) for k in hw if hg.get(k) != hw[k]}
+        raise AssertionError(f"blob mismatch: {_first_diff(got, want)}; header diff {diff}")
+    ref = O.decompress(want, p_np)
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    rec = N.decompress(blob, p_dev, header=hb, status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert np.array_equal(_u(rec.cpu().numpy()), _u(ref)), "decompression mismatch"
+    for s, c in ranges:
+        seg = N.decompress_range(blob, p_dev[s: s + c], s, c, header=hb, status=status)
+        torch.cuda.synchronize()
+        assert np.array_equal(_u(seg.cpu().numpy()), _u(ref[s: s + c])), (s, c)
+    assert int(status.item()) == 0
+    return O.parse_header(want), rec
+
+
+# ---------------------------------------------------------------------------------------
+# the plain 1-D pair at full size (2^20 float64), both anchors
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("anchor", [N.ANCHOR_ZERO, N.ANCHOR_MIN])
+def test_plain_pair_full_size(anchor):
+    p, x = synth.plain_pair(1 << 20)
+    rng = np.random.default_rng(0)
+    ranges = [(0, 1 << 20), (12345, 777), (4095, 2), (1 << 19, 1 << 18)]
+    ranges += [(int(s), int(rng.integers(1, 50000))) for s in rng.integers(0, 1 << 19, 6)]
+    h, _ = check_pair(p.numpy(), x.numpy(), 1e-3, 8, anchor=anchor, ranges=ranges)
+    assert h["n_sel"] == 255 and 0.05 < h["n_inc"] / h["n"] < 0.08
+
+
+@pytest.mark.parametrize("B", [6, 10])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_plain_pair_dtypes_and_widths(B, dtype):
+    p, x = synth.plain_pair(300_001, dtype=dtype, seed=synth.seed_for(0, B))
+    check_pair(p.numpy(), x.numpy(), 1e-3, B, ranges=[(0, 300_001), (299_000, 1001)])
+
+
+# ---------------------------------------------------------------------------------------
+# FLASH-like 3-D series (scaled), closed loop: prev = previous reconstruction
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("E,B", [(1e-3, 8), (1e-4, 10), (1e-4, 8), (1e-3, 10)])
+def test_flash_series_closed_loop(E, B):
+    steps = synth.flash_series(side=96, steps=4, device=DEV)
+    prev = steps[0]
+    for t in range(1, 4):
+        cur = steps[t]
+        h, rec = check_pair(prev.cpu().numpy(), cur.cpu().numpy(), E, B,
+                            ranges=[(1000, 50_000)], p_dev=prev, x_dev=cur)
+        assert 0.001 < h["n_inc"] / h["n"] < 0.2     # shocks: 5% of cells, U(-0.5, 2)
+        prev = rec
+
+
+# ---------------------------------------------------------------------------------------
+# CMIP-like 2-D float32 fields: full 3600 x 1800 grid, three monthly pairs
+# ---------------------------------------------------------------------------------------
+def test_climate_full_grid():
+    months = dict(synth.climate_series(steps=4, device=DEV))
+    for t in range(1, 4):
+        p, x = months[t - 1], months[t]
+        h, _ = check_pair(p.cpu().numpy(), x.cpu().numpy(), 1e-3, 8,
+                          ranges=[(0, 64), (3_000_000, 100_000)], p_dev=p, x_dev=x)
+        assert h["n_inc"] / h["n"] >= 0.03          # the ocean mask alone is 3%
+
+
+# ---------------------------------------------------------------------------------------
+# adversarial inputs
+# ---------------------------------------------------------------------------------------
+def _edge_case_arrays(T, n=50_000, seed=5):
+    rng = np.random.default_rng(seed)
+    E = 2.0 ** -10
+    w = 2 * E
+    p = rng.lognormal(size=n).astype(T)
+    # ratios exactly on bin edges, on centres, and a few ulps either side
+    m = rng.integers(-300, 300, n)
+    base = (-E + m * w)
+    jitter = rng.choice([0.0, 1.0, -1.0, 0.5, -0.5], n) * np.finfo(T).eps
+    r = (base + jitter).astype(T)
+    x = (p * (T(1) + r)).astype(T)
+    k = n // 20
+    sel = rng.permutation(n)
+    # special values
+    p[sel[0:k]] = 0
+    x[sel[k:2 * k]] = 0
+    p[sel[2 * k:2 * k + 50]] = np.inf
+    x[sel[2 * k + 50:2 * k + 100]] = -np.inf
+    x[sel[2 * k + 100:2 * k + 150]] = np.nan
+    p[sel[2 * k + 150:2 * k + 200]] = -p[sel[2 * k + 150:2 * k + 200]]
+    tiny = np.finfo(T).smallest_subnormal
+    p[sel[2 * k + 200:2 * k + 250]] = tiny * 3
+    x[sel[2 * k + 250:2 * k + 300]] = tiny * 5
+    p[sel[2 * k + 300:2 * k + 350]] = -0.0
+    # ratios near the cap 2^21 * w and beyond
+    cap = T(w) * T(2 ** 21)
+    for i, f in enumerate((1.0, 1.0 - 1e-6, 1.0 + 1e-6, 0.5, 2.0)):
+        j = sel[2 * k + 350 + 10 * i: 2 * k + 360 + 10 * i]
+        p[j] = 1
+        x[j] = T(1) + T(cap * f)
+    return p, x, E
+
+
+@pytest.mark.parametrize("T", [np.float32, np.float64])
+@pytest.mark.parametrize("anchor", [N.ANCHOR_ZERO, N.ANCHOR_MIN])
+def test_adversarial_edges_and_specials(T, anchor):
+    p, x, E = _edge_case_arrays(T)
+    nanpay = np.array([0x7FF8DEADBEEF0001 if T == np.float64 else 0x7FC0BEEF],
+                      dtype=np.uint64 if T == np.float64 else np.uint32).view(T)[0]
+    x[7] = nanpay
+    check_pair(p, x, E, 9, anchor=anchor, ranges=[(0, 50_000), (3, 4000)])
+
+
+@pytest.mark.parametrize("B", [1, 2, 3, 5, 7, 8, 11, 13, 16])
+def test_all_widths_small_blocks(B):
+    """Index widths whose blocks do not hold a multiple of 32 indices; many blocks and
+    sub-blocks, partial last sub-block in every block."""
+    p, x = synth.plain_pair(123_457, seed=synth.seed_for(0, 100 + B))
+    bb = 3001                                   # epb = 24008 // B
+    rng = np.random.default_rng(B)
+    ranges = [(int(s), int(rng.integers(1, 9000))) for s in rng.integers(0, 110_000, 8)]
+    check_pair(p.numpy(), x.numpy(), 1e-3, B, block_bytes=bb, ranges=ranges)
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 31, 32, 33, 4095, 4096, 4097, 8191, 65537])
+def test_sizes(n):
+    p, x = synth.plain_pair(max(n, 1), seed=synth.seed_for(0, 7))
+    p, x = p[:n].numpy().copy(), x[:n].numpy().copy()
+    check_pair(p, x, 1e-3, 8, ranges=[(0, n), (n // 2, n - n // 2)])
+
+
+def test_many_ties_in_counts():
+    """Every bin holds the same count: the selection is decided by the tie-break alone."""
+    n = 64 * 1000
+    E = 2.0 ** -8
+    m = np.repeat(np.arange(-500, 500), 64)
+    rng = np.random.default_rng(9)
+    rng.shuffle(m)
+    p = np.ones(n)
+    x = 1 + m * (2 * E)
+    for B in (4, 8, 10):
+        h, _ = check_pair(p, x, E, B)
+        assert h["n_sel"] == min(1000, (1 << B) - 1)
+
+
+def test_all_non_finite_and_constant():
+    n = 10_000
+    p = np.full(n, np.nan)
+    check_pair(p, p.copy(), 1e-3, 8)
+    q = np.full(n, 3.5)
+    h, rec = check_pair(q, q.copy(), 1e-3, 8)
+    assert h["n_inc"] == 0 and h["n_sel"] == 1
+
+
+def test_misaligned_views_take_the_scalar_path():
+    p, x = synth.plain_pair(100_003, seed=synth.seed_for(0, 11))
+    pd, xd = p.to(DEV), x.to(DEV)
+    # one-element offsets: 8-byte aligned but not 16-byte aligned
+    check_pair(p[1:].numpy().copy(), x[1:].numpy().copy(), 1e-3, 8, p_dev=pd[1:], x_dev=xd[1:])
+    p32, x32 = p.float(), x.float()
+    check_pair(p32[3:].numpy().copy(), x32[3:].numpy().copy(), 1e-3, 8,
+               p_dev=p32.to(DEV)[3:], x_dev=x32.to(DEV)[3:])
+
+
+def test_worked_example_golden(golden_dir):
+    import json
+    import os
+    g = json.load(open(os.path.join(golden_dir, "worked_example.json")))
+    p = np.array(g["prev"], dtype=np.float64)
+    x = np.array(g["cur"], dtype=np.float64)
+    for anchor in (N.ANCHOR_ZERO, N.ANCHOR_MIN):
+        for bb in (16, g["block_bytes_small"]):
+            _, rec = check_pair(p, x, g["E"], g["B"], anchor=anchor, block_bytes=bb)
+            assert rec.cpu().numpy().tolist() == g["recon"]
+
+
+def test_repeatable_and_workspace_reuse():
+    """Same inputs -> same bytes, across workspace reuse with other sizes and dtypes in between
+    (the workspace is left ready for the next call)."""
+    p, x = synth.plain_pair(200_000, seed=synth.seed_for(0, 13))
+    pd, xd = p.to(DEV), x.to(DEV)
+    _, _, first = gpu_compress(pd, xd, 1e-3, 8)
+    q, y = synth.plain_pair(77_777, dtype=torch.float32, seed=synth.seed_for(0, 14))
+    gpu_compress(q.to(DEV), y.to(DEV), 1e-4, 10, anchor=N.ANCHOR_MIN)
+    _, _, second = gpu_compress(pd, xd, 1e-3, 8)
+    assert first == second
