@@ -204,6 +204,34 @@ int numarck_compress(const void* prev, const void* cur, int64_t n, const numarck
                      void* blob, size_t blob_cap, void* ws, size_t ws_bytes,
                      numarck_stream_t stream);
 
+/* ---- compression without a workspace argument ----
+ * The paper has no counterpart to this entry point; it exists for callers that cannot allocate
+ * device memory: a simulation that has handed all of HBM to its own pool (in-situ checkpoint
+ * compression), code that must not take the implicit device synchronisation of
+ * cudaMalloc/cudaFree, or plugins whose host application forbids raw CUDA allocations.
+ *
+ * Same arguments, results and errors as numarck_compress, minus the workspace: the scratch
+ * memory is one fixed array of NUMARCK_NOALLOC_SCRATCH_BYTES (48 MiB) inside the library's
+ * device image. Once the library's device code is loaded on a GPU (at the latest at the first
+ * call of this entry point there), that GPU holds the array until the process exits. The call
+ * allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Limit: (n, p) is accepted only if numarck_workspace_bytes(n, p) <=
+ * NUMARCK_NOALLOC_SCRATCH_BYTES; otherwise NUMARCK_ERR_CAPACITY is returned before any launch.
+ * The fixed part of the workspace is about 41 MiB; the rest holds 8 bytes per 4096-element
+ * sub-block, so with the default 1 MB index blocks n up to about 3.7 * 10^9 elements is
+ * accepted; smaller blocks lower the limit.
+ *
+ * First call on a device: it looks up the array's device address with that device current and
+ * clears the whole array on `stream`. Make that first call before any stream capture.
+ * Every call shares the one array, which keeps the last call's contents; each call clears the
+ * part that must start at zero. Calls that overlap on the GPU (different streams, or several
+ * host threads without ordering) race on the array: serialise them. */
+#define NUMARCK_NOALLOC_SCRATCH_BYTES (48 * 1024 * 1024)
+int numarck_compress_noalloc(const void* prev, const void* cur, int64_t n,
+                             const numarck_params* p, void* blob, size_t blob_cap,
+                             numarck_stream_t stream);
+
 /* ---- header inspection (host only) ----
  * header_host: a HOST copy of (at least) the first NUMARCK_HEADER_BYTES bytes of a blob,
  * taken after the compressing stream has been synchronised.
