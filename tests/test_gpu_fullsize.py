@@ -101,8 +101,8 @@ def test_fullsize_flash_pair(series, E, B):
     # 2. sampled indices, computed by the oracle one by one
     rng = np.random.default_rng(1)
     sub = h["sub"]
-    edges = np.concatenate([np.arange(0, n, h["epb"])[:, None] + np.arange(-3, 3)[None, :],
-                            np.arange(0, n, sub * 977)[:, None] + np.arange(-2, 2)[None, :]]).ravel()
+    edges = np.concatenate([(np.arange(0, n, h["epb"])[:, None] + np.arange(-3, 3)[None, :]).ravel(),
+                            (np.arange(0, n, sub * 977)[:, None] + np.arange(-2, 2)[None, :]).ravel()])
     j = np.unique(np.clip(np.concatenate([rng.integers(0, n, 1 << 20), edges, [0, n - 1]]), 0, n - 1))
     jt = torch.from_numpy(j).to(DEV)
     ps = p_dev[jt].cpu().numpy()
@@ -115,7 +115,6 @@ def test_fullsize_flash_pair(series, E, B):
 
     # 3. properties over every point
     M = (1 << B) - 1
-    marker = torch.from_numpy(np.zeros(0, dtype=bool))
     # per-element indices on the device: unpack with the same reader logic in torch
     jj = torch.arange(n, device=DEV, dtype=torch.int64)
     idx_off = torch.from_numpy(np.frombuffer(
