@@ -34,6 +34,7 @@ METRIC = "compress+decompress input GB/s (and % of HBM peak) on 1 GB300, bit-exa
 WORKLOAD = ("FLASH-like 3-D float64 field 1024^3 (8 GiB/step), 4 timesteps, 3 closed-loop pairs "
             "x E{1e-3,1e-4} x B{8,10}")
 KERNEL_FILES = {"k3_assign": ["k_assign.cu", "common.cuh"],
+                "k3_exact": ["k_assign.cu", "common.cuh"],
                 "k1_hist": ["k_hist.cu", "common.cuh"],
                 "k4_decode": ["k_decode.cu", "common.cuh"]}
 
@@ -266,7 +267,7 @@ def main():
             prev = xs[0]
             for t in range(1, 4):
                 if trace:
-                    N.trace_events(new_events(4))
+                    N.trace_events(new_events(6))
                 N.compress(prev, xs[t], E, B, blob=blob, workspace=ws)
                 if trace:
                     N.trace_events(new_events(2))
@@ -301,32 +302,35 @@ def main():
     bytes_rank = args.steps * n_pairs * n * 8
     value = _sum_over_ranks(dist, bytes_rank) / (ms_total / 1e3) / 1e9
 
-    # per-kernel times from the trace events (compress: K1, K2, K3; decompress: K4)
-    k1 = k2 = k3 = k4 = 0.0
+    # per-kernel times from the trace events: compress K1, K2, K3a, K3b, K3c; decompress K4
+    kt = {"k1_hist": 0.0, "k2_topk": 0.0, "k3_assign": 0.0, "k3_scan": 0.0, "k3_exact": 0.0,
+          "k4_decode": 0.0}
     nc = nd = 0
     for evs in ev_pool:
-        if len(evs) == 4:
-            k1 += evs[0].elapsed_time(evs[1])
-            k2 += evs[1].elapsed_time(evs[2])
-            k3 += evs[2].elapsed_time(evs[3])
+        if len(evs) == 6:
+            for name, (a, b) in (("k1_hist", (0, 1)), ("k2_topk", (1, 2)), ("k3_assign", (2, 3)),
+                                 ("k3_scan", (3, 4)), ("k3_exact", (4, 5))):
+                kt[name] += evs[a].elapsed_time(evs[b])
             nc += 1
         else:
-            k4 += evs[0].elapsed_time(evs[1])
+            kt["k4_decode"] += evs[0].elapsed_time(evs[1])
             nd += 1
-    # algorithmic bytes per launch (HBM roofline); n_inc / B from the last blob of each combo
+    avg = {k: (v / nd if k == "k4_decode" else v / nc) for k, v in kt.items()}
+    # algorithmic bytes per launch (HBM roofline); n_inc / B from the last blob of the step
     hdr = N.parse_header(N.header_bytes(blob))
     alpha = hdr["n_inc"] / n
     Bl = hdr["B"]
     alg = {"k1_hist": 2 * 8 * n,
-           "k3_assign": 2 * 8 * n + n * Bl / 8 + alpha * n * 8,
+           "k3_assign": 2 * 8 * n + n * Bl / 8,
+           "k3_exact": 2 * alpha * n * 8,
            "k4_decode": (1 - alpha) * n * 8 + n * Bl / 8 + alpha * n * 8 + n * 8}
-    avg = {"k1_hist": k1 / nc, "k3_assign": k3 / nc, "k4_decode": k4 / nd}
-    dominant = max(avg, key=avg.get)
+    dominant = max(alg, key=lambda k: avg[k])
     peak, peak_kind = _peaks()
     achieved = alg[dominant] / (avg[dominant] / 1e3) / 1e9
-    kernel_ms = {"k1_hist": round(k1 / nc, 4), "k2_topk": round(k2 / nc, 4),
-                 "k3_assign": round(k3 / nc, 4), "k4_decode": round(k4 / nd, 4)}
+    kernel_ms = {k: round(v, 4) for k, v in avg.items()}
     kernel_gbs = {k: round(alg[k] / (avg[k] / 1e3) / 1e9, 1) for k in alg}
+    t_comp = sum(avg[k] for k in ("k1_hist", "k2_topk", "k3_assign", "k3_scan", "k3_exact"))
+    comp_alg = 4 * 8 * n + n * Bl / 8 + alpha * n * 8
 
     # end to end through the public API with host buffers: every pair copies its current
     # timestep host->device (pinned), compresses, copies the used blob bytes and the
@@ -398,10 +402,11 @@ def main():
                          "frac": achieved / peak, "traffic": _traffic(dominant, side),
                          "algorithmic_bytes_per_launch": alg[dominant]},
             "kernels_ms": kernel_ms, "kernels_gbs": kernel_gbs,
-            "compress_gbs": n * 8 / ((k1 + k2 + k3) / nc / 1e3) / 1e9,
-            "decompress_gbs": n * 8 / (k4 / nd / 1e3) / 1e9,
+            "compress_gbs": n * 8 / (t_comp / 1e3) / 1e9,
+            "compress_path_hbm_frac": comp_alg / (t_comp / 1e3) / 1e9 / peak,
+            "decompress_gbs": n * 8 / (avg["k4_decode"] / 1e3) / 1e9,
             "alpha_last": alpha, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
-            "gpu_launches": args.steps * n_pairs * 4,
+            "gpu_launches": args.steps * n_pairs * 6,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

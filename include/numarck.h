@@ -279,10 +279,11 @@ int numarck_decompress_range(const void* blob, const void* header_host,
 /* ---- tracing (kernel-level timing for profilers and benchmarks) ----
  * events : an array of `count` cudaEvent_t handles owned by the caller, or NULL to stop.
  * While set, every numarck_compress call made on this host thread records, on its stream,
- * events[0] before its first kernel and events[1], events[2], events[3] after the ratio +
- * histogram kernel(s), the top-k kernel and the assign + pack kernel; every
- * numarck_decompress[_range] call records events[0] before and events[1] after its kernel.
- * A call needs count >= 4 (compress) or >= 2 (decompress) to record anything.
+ * events[0] before its first kernel and events[1..5] after, in order, the ratio + histogram
+ * kernel(s), the top-k kernel, the assign + pack kernel, the offset-table scan and the
+ * incompressible-value copy; every numarck_decompress[_range] call records events[0] before and
+ * events[1] after its kernel. A call needs count >= 6 (compress) or >= 2 (decompress) to record
+ * anything.
  * Returns NUMARCK_ERR_INVALID_ARG if count < 0. */
 int numarck_trace_events(void* const* events, int count);
 

@@ -1,8 +1,8 @@
 // capi.cu — the extern "C" boundary of the NUMARCK library (declared in include/numarck.h).
 //
 // Host side only: argument validation, blob geometry (§IV.C block layout, §IV.D arrays),
-// workspace layout, and the launch sequence K0 (ANCHOR_MIN) -> K1 -> K2 -> K3 for compression
-// and K4 for (partial) decompression. Nothing here allocates device memory.
+// workspace layout, and the launch sequence K0 (ANCHOR_MIN) -> K1 -> K2 -> K3a -> K3b -> K3c for
+// compression and K4 for (partial) decompression. Nothing here allocates device memory.
 #include <cmath>
 #include <cstddef>
 #include <cstring>
@@ -79,8 +79,7 @@ Consts<T> make_consts(double E, int anchor) {
   c.Ef = (float)c.E_T;
   c.cap_lo = f_down((double)c.cap * (1.0 - 0x1p-19));
   c.cap_hi = f_up((double)c.cap * (1.0 + 0x1p-19));
-  c.K1 = f_up(0x1p-20 * (double)c.inv_w);
-  c.K0 = f_up(0x1p-22 * (double)c.inv_w * std::fabs((double)c.a) + 0x1p-100);
+  c.K0 = f_up(0x1p-19 * (double)c.inv_w * std::fabs((double)c.a) + 0x1p-60);
   return c;
 }
 
@@ -228,15 +227,19 @@ int numarck_compress(const void* prev, const void* cur, int64_t n, const numarck
   h.total_bytes = g.off_exact;
 
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  trace(0, 4, s);
+  trace(0, 6, s);
   if (p->anchor == NUMARCK_ANCHOR_MIN && launch_anchor_min(P, s) != cudaSuccess)
     return NUMARCK_ERR_CUDA;
   if (launch_hist(P, s) != cudaSuccess) return NUMARCK_ERR_CUDA;
-  trace(1, 4, s);
+  trace(1, 6, s);
   if (launch_topk(P, s) != cudaSuccess) return NUMARCK_ERR_CUDA;
-  trace(2, 4, s);
+  trace(2, 6, s);
   if (launch_assign(P, s) != cudaSuccess) return NUMARCK_ERR_CUDA;
-  trace(3, 4, s);
+  trace(3, 6, s);
+  if (launch_offsets(P, s) != cudaSuccess) return NUMARCK_ERR_CUDA;
+  trace(4, 6, s);
+  if (launch_exact(P, s) != cudaSuccess) return NUMARCK_ERR_CUDA;
+  trace(5, 6, s);
   return NUMARCK_OK;
 }
 

@@ -30,6 +30,12 @@ constexpr int TILE_THREADS = 512;               // K3/K4 block size
 constexpr int EPT = SUB / TILE_THREADS;         // elements per thread per tile (8)
 constexpr int NCHUNK = EPT * (TILE_THREADS / 32); // 32-element chunks per tile (128)
 constexpr unsigned KEY_BIAS = 0x40000000u;      // bin-range keys: 0 means "no value"
+// Per-element bin codes written by K1 and read by K3: code = bin - code_base for bins within
+// 65534 of code_base (code_base = zero-change bin - 32767); CODE_FAR for binnable points outside
+// that window (K3 classifies them again), CODE_NONE for points that are not binnable.
+constexpr unsigned CODE_FAR = 0xFFFEu;
+constexpr unsigned CODE_NONE = 0xFFFFu;
+constexpr int CODE_HALF = 32767;
 
 // Workspace control block (first 256 bytes of the workspace). Zero at entry of every
 // compression; the kernels restore the zero state of every field they accumulate into.
@@ -46,7 +52,8 @@ struct Ctrl {
   int pad0;
   double a;                     // grid anchor (the T value, widened)
   unsigned int win_err;         // a bin fell outside the histogram window (never expected)
-  unsigned int pad1[49];
+  int code_base;                // bin of code 0 in K1's per-element bin codes (written by K1)
+  unsigned int pad1[48];
 };
 static_assert(sizeof(Ctrl) == 256, "Ctrl must be 256 bytes");
 
@@ -102,6 +109,14 @@ __host__ __device__ inline Geometry make_geometry(int64_t n, int dtype, int B, i
 
 constexpr int64_t MAX_N = (int64_t)1 << 40;
 
+// Byte offset of K1's per-element bin codes inside the blob buffer: the tail of the
+// incompressible-value capacity (element j at + 2j). Incompressible values written for the
+// elements before any index j_e take at most j_e * L bytes, and j_e * (L - 2) <= n * (L - 2), so
+// they never reach the code of an element at or after j_e.
+__host__ __device__ __forceinline__ int64_t code_offset(const Geometry& g) {
+  return g.off_exact + g.n * ((g.dtype == NUMARCK_F64 ? 8 : 4) - 2);
+}
+
 // Checks a header against the geometry its own fields imply. Returns 0 or NUMARCK_ERR_CORRUPT
 // (or the header's non-zero device status).
 __host__ __device__ inline int check_header(const numarck_header& h, Geometry* out) {
@@ -132,9 +147,9 @@ struct Consts {
   T E_T, w, inv_w, cap, a;
   int hbase;      // histogram window index = bin - hbase
   // float64 estimate: af = fl32(a), inv_wf = fl32(inv_w), Ef = fl32(E_T),
-  // cap_lo <= cap (1 - 2^-19), cap_hi >= cap (1 + 2^-19), K1 >= 2^-20 inv_w,
-  // K0 >= 2^-23 inv_w |a| + 2^-100 (all rounded away from the decision)
-  float af, inv_wf, Ef, cap_lo, cap_hi, K1, K0;
+  // cap_lo <= cap (1 - 2^-19), cap_hi >= cap (1 + 2^-19),
+  // K0 >= 2^-19 inv_w |a| + 2^-60 (all rounded away from the decision)
+  float af, inv_wf, Ef, cap_lo, cap_hi, K0;
 };
 
 // ------------------------------------------------------------------------------------------
@@ -237,106 +252,105 @@ static __device__ __noinline__ bool check_exact_f64_slow(double p, double x, dou
 // ------------------------------------------------------------------------------------------
 // float64 filter-and-refine.
 //
-// Fast path applies when p and x are normal with biased exponents in [100, 1940] and differ
-// by at most 9 (|x/p| in (2^-10, 2^10)); everything else takes the exact float64 path.
-// Let s = 2^(ep-1023). Then
-//   d/s  = (x - p)/s is computed EXACTLY as a 64-bit integer (aligned mantissas, < 2^62) and
-//          truncated to 24 bits:            df = (d/s)(1 - tau),  0 <= tau < 2^-23
-//   |p|/s = 1.mantissa(p) truncated:         pf = (|p|/s)(1 - tau'), 0 <= tau' < 2^-23
-//   Df = __fdividef(df, pf) * sign(p):  |Df - D*| <= 2^-21 |D*|   (2-ulp divide), D* = d/p real
-// The exact float64 chain (two roundings to the ratio, one each to t and u) satisfies
-//   |u64 - U| <= 2.01 * 2^-53 (|U| + inv_w |D*|),   U = (D* - a) inv_w (real),
+// Fast path: p normal with biased exponent ep in [200, 1940] and x finite. With s = 2^(ep-1023):
+//   d64 = fl64(x - p)                       (one DSUB; |d64 - d| <= 2^-53 |d|)
+//   df  = d64/s truncated to 24 bits         (bit assembly; relative error < 2^-23;
+//                                             |d/s| < 2^-126, which includes every subnormal
+//                                             d64 since ep >= 200, is taken as 0)
+//   pf  = |p|/s = 1.mantissa(p) truncated    (relative error < 2^-23)
+//   Df  = fl32(df * rcp.approx(pf)) * sign(p) (rcp.approx: absolute error 2^-23 on [1, 2))
+// so |Df - D*| <= 2^-20.8 |D*| + 2^-126 with D* = (x - p)/p exactly. The exact float64 chain
+// (two roundings to the ratio, one each to t and u) satisfies
+//   |u64 - U| <= 2.01 * 2^-53 (|U| + inv_w |D*|),   U = (D* - a) inv_w,
 // and the float32 chain tf = fl(Df - af), uf = fl(tf * inv_wf) satisfies
-//   |uf - U| <= 3.01 * 2^-24 |U| + inv_w (2^-21 |D*| + 2^-24 |a|) (1 + 2^-22).
-// Hence |uf - u64| <= eps = 2^-20 inv_w |Df| + 2^-22 |uf| + 2^-23 inv_w |a| (+ 2^-100),
-// evaluated with upward rounding (each term carries a factor >= 2 of slack). When
-// floor(uf - eps) == floor(uf + eps) (downward / upward rounded), that floor IS floor(u64).
-// The cap test is decided the same way with the 2^-19 margins in cap_lo / cap_hi.
+//   |uf - U| <= 3.01 * 2^-24 |U| + inv_w (2^-20.8 |D*| + 2^-24 |a| + 2^-126).
+// Using inv_w |D*| <= (|uf| + inv_w |a|)(1 + 2^-20), everything is bounded by
+//   eps = 1.5 * 2^-20 |uf| + (2^-19 inv_w |a| + 2^-60)     (one FMA rounded upward)
+// When floor(uf - eps) == floor(uf + eps) (rounded downward / upward), that floor is
+// floor(u64), the exact float64 bin. The cap test uses margins 2^-19 the same way.
 // ------------------------------------------------------------------------------------------
-struct Est {
-  float df;     // (x - p)/s, signed
-  float pf;     // |p|/s in [1, 2)
-  float xf;     // |x|/s
-  int psign;    // sign bit of p
-  int fast;     // 1 if the estimate decided the bin (df/pf/xf valid)
-};
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 
-__device__ __forceinline__ int classify_f64(double p, double x, const Consts<double>& c, int& b,
-                                            Est& est) {
-  est.fast = 0;
-  const unsigned long long pb = (unsigned long long)__double_as_longlong(p);
-  const unsigned long long xb = (unsigned long long)__double_as_longlong(x);
-  const int ep = (int)((pb >> 52) & 0x7FF);
-  const int ex = (int)((xb >> 52) & 0x7FF);
-  // p = +-0: ratio is +-inf or NaN; any non-finite input: ratio is inf or NaN.
-  if ((pb << 1) == 0 || ep == 0x7FF || ex == 0x7FF) return 0;
-  const int de = ex - ep;
-  if (ep >= 100 && ex >= 100 && ep <= 1940 && ex <= 1940 && de >= -9 && de <= 9) {
-    const unsigned long long MANT = 0x000FFFFFFFFFFFFFull, HID = 0x0010000000000000ull;
-    const int sx = de > 0 ? de : 0;
-    const int sp = de < 0 ? -de : 0;
-    long long X = (long long)(((xb & MANT) | HID) << sx);
-    long long P = (long long)(((pb & MANT) | HID) << sp);
-    if (xb >> 63) X = -X;
-    if (pb >> 63) P = -P;
-    const long long Di = X - P;  // d = Di * 2^(min(ex,ep) - 1075), exactly
-    float df = 0.0f;
-    if (Di != 0) {
-      const unsigned long long mag = Di < 0 ? (unsigned long long)(-Di) : (unsigned long long)Di;
-      const int lz = __clzll((long long)mag);
-      const unsigned m24 = (unsigned)((mag << lz) >> 40);
-      const unsigned bexp = (unsigned)((63 - lz) - sp + 75);   // in [66, 137]
-      df = __uint_as_float((bexp << 23) | (m24 & 0x7FFFFFu) | (Di < 0 ? 0x80000000u : 0u));
-    }
-    const float pf = __uint_as_float(0x3F800000u | (unsigned)((pb >> 29) & 0x7FFFFFu));
-    float Df = __fdividef(df, pf);
-    if (pb >> 63) Df = -Df;
+// The float32 ratio estimate Df of the fast path (valid when p has a biased exponent in
+// [200, 1940] and x is finite; see above). Returns false when |d/s| >= 2^128.
+__device__ __forceinline__ bool ratio_estimate(unsigned ph, unsigned pl, int ep, double p, double x,
+                                               float& Df) {
+  const double d = __dsub_rn(x, p);
+  const unsigned dh = (unsigned)__double2hiint(d), dl = (unsigned)__double2loint(d);
+  const int e32 = (int)((dh >> 20) & 0x7FFu) - ep + 127;
+  const unsigned dmant = __funnelshift_r(dl, dh, 29) & 0x7FFFFFu;
+  const unsigned dsign = dh & 0x80000000u;
+  const float df = __uint_as_float(e32 > 0 ? (dsign | ((unsigned)e32 << 23) | dmant) : dsign);
+  const float pf = __uint_as_float(0x3F800000u | (__funnelshift_r(pl, ph, 29) & 0x7FFFFFu));
+  Df = __uint_as_float(__float_as_uint(__fmul_rn(df, rcp_approx(pf))) ^ (ph & 0x80000000u));
+  return e32 < 255;
+}
+
+// Bin of (p, x) for float64: 1 and the bin if binnable, else 0. Equal to classify_exact<double>.
+__device__ __forceinline__ int classify_f64(double p, double x, const Consts<double>& c, int& b) {
+  const unsigned ph = (unsigned)__double2hiint(p), pl = (unsigned)__double2loint(p);
+  const unsigned xh = (unsigned)__double2hiint(x);
+  const int ep = (int)((ph >> 20) & 0x7FFu);
+  const int ex = (int)((xh >> 20) & 0x7FFu);
+  if ((unsigned)(ep - 200) <= 1740u && ex != 0x7FF) {
+    float Df;
+    if (!ratio_estimate(ph, pl, ep, p, x, Df)) return 0;   // |d/s| >= 2^128: far beyond the cap
     const float aD = fabsf(Df);
-    if (aD > c.cap_hi) return 0;                 // certainly |ratio| > cap
-    if (aD <= c.cap_lo) {                        // certainly binnable
-      const float tf = __fsub_rn(Df, c.af);
-      const float uf = __fmul_rn(tf, c.inv_wf);
-      const float eps = __fadd_ru(__fadd_ru(__fmul_ru(c.K1, aD), __fmul_ru(0x1p-22f, fabsf(uf))),
-                                  c.K0);
+    if (aD > c.cap_hi) return 0;                           // certainly |ratio| > cap
+    if (aD <= c.cap_lo) {                                  // certainly binnable
+      const float uf = __fmul_rn(__fsub_rn(Df, c.af), c.inv_wf);
+      const float eps = __fmaf_ru(0x1.8p-20f, fabsf(uf), c.K0);
       const float lo = floorf(__fsub_rd(uf, eps));
       const float hi = floorf(__fadd_ru(uf, eps));
-      if (lo == hi) {
-        b = (int)lo;
-        est.fast = 1;
-        est.df = df;
-        est.pf = pf;
-        est.psign = (int)(pb >> 63);
-        est.xf = __uint_as_float(((unsigned)(de + 127) << 23) | (unsigned)((xb >> 29) & 0x7FFFFFu));
+      if (lo == hi && lo < 4194304.0f) {
+        b = __float_as_int(__fadd_rn(lo, 12582912.0f)) - 0x4B400000;   // exact for |lo| < 2^22
         return 1;
       }
     }
+  } else if ((ph << 1) == 0u && pl == 0u) {
+    return 0;                                              // p = +-0: ratio is +-inf or NaN
+  } else if (ep == 0x7FF || ex == 0x7FF) {
+    return 0;                                              // non-finite input
   }
   return classify_exact_f64_slow(p, x, c, &b);
 }
 
-// Error-bound check for float64 with the estimate of classify_f64.
-// With e* = p*m - x = p*c' - d (c' = m - 1 exactly, real), in units of s:
-//   pc = fl32(sign(p) pf * cf), cf = fl32(fl64(m - 1)):  |pc - p c'/s| <= 2^-22 |pc| (1+2^-21)
-//   ef = fl32(pc - df):   |ef - e*/s| <= 2^-21|pc| + 2^-22|df| + 2^-23|ef| =: beta
-//   float64: |e64 - e*|/s <= 2^-50 (pf (1 + |cf|) + |ef|) (one rounding in p*m, one in R - x)
-//   tolf = fl32(Ef * xf):  tol64/s in [tolf (1 - 2^-21), tolf (1 + 2^-21)]
-// so |ef| + beta' < tolf (1 - 2^-21) proves |e64| <= tol64, and |ef| - beta' > tolf (1 + 2^-21)
-// proves the opposite; otherwise the exact float64 check decides.
+// Error-bound check of §III.C for float64 points in a selected bin, decided in ratio space.
+// Dividing the exact check |fl(fl(p*m) - x)| <= fl(E_T*|x|) by |p| gives, with
+// G* = c' - D* (c' = m - 1 exactly, D* = (x - p)/p) and H* = E_T |1 + D*|:
+//   ok  <=>  |G* + eta| <= H* (1 + theta),  |eta| <= 2^-52 (|m| + |G*|),  |theta| <= 2^-53.
+// The float32 estimates G = fl(cf - Df), cf = fl32(fl64(m - 1)), and
+// H = fl(Ef * |fl(1 + Df)|) satisfy
+//   |G - G*| <= 2^-23.9 |cf| + 2^-20.7 |Df| + 2^-24 |G| + 2^-125,
+//   |H - H*| <= 3 * 2^-24 H + 2^-20.7 E_T |Df|.
+// delta = 2^-23 (|cf| + |G|) + 2^-20 |Df| + 2^-50 |cf| + 2^-49 covers the first line and eta;
+// deltaH = 2^-21 H + 2^-20 Ef |Df| + 2^-100 covers the second. If |G| + delta < H - deltaH the
+// exact check passes; if |G| - delta > H + deltaH it fails; otherwise the exact float64 check
+// decides. (All bound arithmetic rounds away from the decision.)
 __device__ __forceinline__ bool check_f64(double p, double x, double m, float cf,
-                                          const Consts<double>& c, const Est& est) {
-  if (est.fast) {
-    const float ps = est.psign ? -est.pf : est.pf;
-    const float pc = __fmul_rn(ps, cf);
-    const float ef = __fsub_rn(pc, est.df);
-    const float tolf = __fmul_rn(c.Ef, est.xf);
-    const float aef = fabsf(ef);
-    const float beta = __fadd_ru(
-        __fadd_ru(__fmul_ru(0x1p-21f, fabsf(pc)), __fmul_ru(0x1p-22f, fabsf(est.df))),
-        __fadd_ru(__fmul_ru(0x1p-23f, aef),
-                  __fmul_ru(0x1p-50f, __fadd_ru(__fmul_ru(est.pf, __fadd_ru(1.0f, fabsf(cf))),
-                                                aef))));
-    if (__fadd_ru(aef, beta) < __fmul_rd(tolf, 1.0f - 0x1p-21f)) return true;
-    if (__fsub_rd(aef, beta) > __fmul_ru(tolf, 1.0f + 0x1p-21f)) return false;
+                                          const Consts<double>& c) {
+  const unsigned ph = (unsigned)__double2hiint(p), pl = (unsigned)__double2loint(p);
+  const unsigned xh = (unsigned)__double2hiint(x);
+  const int ep = (int)((ph >> 20) & 0x7FFu);
+  const int ex = (int)((xh >> 20) & 0x7FFu);
+  if ((unsigned)(ep - 200) <= 1740u && (unsigned)(ex - 100) <= 1840u) {
+    float Df;
+    if (ratio_estimate(ph, pl, ep, p, x, Df)) {
+      const float aDf = fabsf(Df);
+      const float G = __fsub_rn(cf, Df);
+      const float aG = fabsf(G);
+      const float H = __fmul_rn(c.Ef, fabsf(__fadd_rn(1.0f, Df)));
+      const float delta = __fmaf_ru(0x1p-23f, __fadd_ru(fabsf(cf), aG),
+                                    __fmaf_ru(0x1p-20f, aDf,
+                                              __fmaf_ru(0x1p-50f, fabsf(cf), 0x1p-49f)));
+      const float dH = __fmaf_ru(0x1p-21f, H, __fmaf_ru(0x1p-20f * c.Ef, aDf, 0x1p-100f));
+      if (__fadd_ru(aG, delta) < __fsub_rd(H, dH)) return true;
+      if (__fsub_rd(aG, delta) > __fadd_ru(H, dH)) return false;
+    }
   }
   return check_exact_f64_slow(p, x, m, c.E_T);
 }

@@ -28,6 +28,7 @@ struct AssignArgs {
   const float* cftab;
   unsigned long long* tstatus;
   unsigned char* blob;
+  const unsigned short* codes;   // K1's per-element bin codes
 };
 
 struct RankView {
@@ -42,17 +43,20 @@ struct RankView {
   }
 };
 
+// Index of one element from its bin code (§III.C): M unless binnable, in a selected bin, and the
+// error check passes. Codes outside the code window are classified again (rare).
 template <typename T>
 struct Assigner;
 
 template <>
 struct Assigner<float> {
-  __device__ __forceinline__ static unsigned run(float p, float x, const Consts<float>& c,
-                                                 const RankView& rv, const float* s_m,
-                                                 const float*, const float* g_m, const float*,
-                                                 unsigned M) {
-    int b = 0;
-    if (!classify_exact<float>(p, x, c, b)) return M;
+  __device__ __forceinline__ static unsigned run(float p, float x, unsigned code, int cbase,
+                                                 const Consts<float>& c, const RankView& rv,
+                                                 const float* s_m, const float*, const float* g_m,
+                                                 const float*, unsigned M) {
+    if (code == CODE_NONE) return M;
+    int b = cbase + (int)code;
+    if (code == CODE_FAR && !classify_exact<float>(p, x, c, b)) return M;
     const unsigned r = rv.lookup(b);
     if (r == M) return M;
     const float m = r < (unsigned)MT_SMEM ? s_m[r] : g_m[r];
@@ -62,19 +66,20 @@ struct Assigner<float> {
 
 template <>
 struct Assigner<double> {
-  __device__ __forceinline__ static unsigned run(double p, double x, const Consts<double>& c,
-                                                 const RankView& rv, const double* s_m,
-                                                 const float* s_cf, const double* g_m,
-                                                 const float* g_cf, unsigned M) {
-    int b = 0;
-    Est est;
-    if (!classify_f64(p, x, c, b, est)) return M;
+  __device__ __forceinline__ static unsigned run(double p, double x, unsigned code, int cbase,
+                                                 const Consts<double>& c, const RankView& rv,
+                                                 const double* s_m, const float* s_cf,
+                                                 const double* g_m, const float* g_cf,
+                                                 unsigned M) {
+    if (code == CODE_NONE) return M;
+    int b = cbase + (int)code;
+    if (code == CODE_FAR && !classify_f64(p, x, c, b)) return M;
     const unsigned r = rv.lookup(b);
     if (r == M) return M;
     const bool sm = r < (unsigned)MT_SMEM;
     const double m = sm ? s_m[r] : g_m[r];
     const float cf = sm ? s_cf[r] : g_cf[r];
-    return check_f64(p, x, m, cf, c, est) ? r : M;
+    return check_f64(p, x, m, cf, c) ? r : M;
   }
 };
 
@@ -93,57 +98,28 @@ struct Bits<double> {
   }
 };
 
-constexpr unsigned long long FLAG_AGG = 1ull << 62;
-constexpr unsigned long long FLAG_INC = 2ull << 62;
-constexpr unsigned long long VAL_MASK = (1ull << 62) - 1;
-constexpr unsigned long long LOOKBACK_LIMIT_NS = 2000000000ull;   // 2 s
 
-// Decoupled look-back (one thread): publish this tile's count, sum predecessors until one
-// with an inclusive prefix is found, publish the inclusive prefix. Returns the exclusive one.
-__device__ long long lookback(unsigned long long* st, long long g, long long count,
-                              int* blob_status) {
-  if (g == 0) {
-    st_relaxed_u64(&st[0], FLAG_INC | (unsigned long long)count);
-    return 0;
-  }
-  st_relaxed_u64(&st[g], FLAG_AGG | (unsigned long long)count);
-  long long P = 0;
-  long long j = g - 1;
-  unsigned long long t0 = 0;
-  unsigned spins = 0;
-  while (j >= 0) {
-    const unsigned long long s = ld_relaxed_u64(&st[j]);
-    const unsigned long long f = s >> 62;
-    if (f == 0) {
-      ++spins;
-      if (spins == 32) t0 = global_timer_ns();
-      if (spins > 32) {
-        __nanosleep(64);
-        if ((spins & 255u) == 0 && global_timer_ns() - t0 > LOOKBACK_LIMIT_NS) {
-          atomicExch(blob_status, NUMARCK_ERR_TIMEOUT);
-          break;
-        }
-      }
-      continue;
-    }
-    P += (long long)(s & VAL_MASK);
-    if (f == 2) break;
-    --j;
-  }
-  st_relaxed_u64(&st[g], FLAG_INC | (unsigned long long)(P + count));
-  return P;
-}
+constexpr int K3_WARPS = 16;                    // warps per CTA; each warp owns whole tiles
+constexpr int K3_THREADS = K3_WARPS * 32;
+constexpr int K3_CHUNK = 1024;                  // elements a warp indexes before packing them
+constexpr int K3_UNROLL = 4;                    // 32-element steps whose loads are in flight
+constexpr int K3_WARP_SMEM = K3_CHUNK * 2;      // per-warp index buffer (bytes)
+constexpr int STEPS = SUB / 32;                 // 32-element steps (= ballot words) per tile
 
+// K3a — indexing and packing. One warp processes one 4096-element tile at a time (tile
+// gw, gw + W, ... for global warp gw of W): for each 1024-element chunk it indexes every
+// element from K1's bin code (coalesced loads of code, p, x; lane l takes every 32nd element),
+// keeps the chunk's indices in its shared buffer and bit-packs them into the index block. It
+// records which points are incompressible as 16-bit half-ballots (half h of 32-element step s at
+// u16 index 2s + h of the tile's own codes, which the tile has already consumed: 4s + 2h < cnt/8
+// bytes < 2 cnt bytes), and the tile's incompressible count in the workspace. There is no
+// dependency between tiles and no block-wide barrier after the table set-up.
 template <typename T>
-__global__ void __launch_bounds__(TILE_THREADS, 2) k3_assign(AssignArgs<T> A) {
-  __shared__ unsigned short s_idx[SUB];
+__global__ void __launch_bounds__(K3_THREADS, 2) k3_assign(AssignArgs<T> A) {
   __shared__ unsigned short s_rank[RW_BINS];
   __shared__ T s_m[MT_SMEM];
   __shared__ float s_cf[MT_SMEM];
-  __shared__ int s_chunk[NCHUNK];
-  __shared__ long long s_tile;
-  __shared__ long long s_P;
-  __shared__ int s_total;
+  extern __shared__ __align__(16) unsigned short k3_idx[];   // [K3_WARPS][K3_CHUNK]
 
   const Geometry& g = A.g;
   Ctrl* ctrl = A.ctrl;
@@ -155,140 +131,200 @@ __global__ void __launch_bounds__(TILE_THREADS, 2) k3_assign(AssignArgs<T> A) {
   if (g.anchor == NUMARCK_ANCHOR_MIN) {
     c.a = (T)ctrl->a;
     c.af = (float)c.a;
-    c.K0 = __fadd_ru(__fmul_ru(__fmul_ru(0x1p-22f, c.inv_wf), fabsf(c.af)), 0x1p-100f);
+    c.K0 = __fadd_ru(__fmul_ru(__fmul_ru(0x1p-18f, c.inv_wf), fabsf(c.af)), 0x1p-60f);
   }
   const int any = ctrl->any;
   const int bmin = ctrl->sel_bmin, bmax = ctrl->sel_bmax, n_sel = ctrl->n_sel;
+  const int cbase = ctrl->code_base;
 
   // shared rank window: the whole bin range if it fits, else centred on the zero-change bin
   int rwlo = bmin;
   if (any && bmax - bmin + 1 > RW_BINS) {
-    int c0 = 0;
-    if (g.anchor == NUMARCK_ANCHOR_MIN)
-      c0 = (int)fmin(fmax(floor(-(double)c.a * (double)c.inv_w), 0.0), (double)(1 << 22));
+    const int c0 = cbase + CODE_HALF;
     rwlo = min(max(c0 - RW_BINS / 2, bmin), bmax - RW_BINS + 1);
   }
-  for (int i = tid; i < RW_BINS; i += TILE_THREADS) {
+  for (int i = tid; i < RW_BINS; i += K3_THREADS) {
     const int b = rwlo + i;
     s_rank[i] = (any && b <= bmax) ? A.rank_of[b - c.hbase] : (unsigned short)M;
   }
   const int nm = min(n_sel, MT_SMEM);
-  for (int r = tid; r < nm; r += TILE_THREADS) {
+  for (int r = tid; r < nm; r += K3_THREADS) {
     s_m[r] = A.mtab[r];
     s_cf[r] = A.cftab[r];
   }
+  __syncthreads();   // the only block-wide barrier: tables are read-only from here on
   const RankView rv{s_rank, A.rank_of, rwlo, c.hbase};
 
-  int* blob_status = reinterpret_cast<int*>(A.blob + offsetof(numarck_header, status));
-  T* exact = reinterpret_cast<T*>(A.blob + g.off_exact);
-  using U = typename Bits<T>::U;
-  U* exact_u = reinterpret_cast<U*>(exact);
-  int64_t* sub_off = reinterpret_cast<int64_t*>(A.blob + g.off_sub_off);
-  int64_t* inc_off = reinterpret_cast<int64_t*>(A.blob + g.off_inc_off);
   const int B = g.B;
-  const int tile_bytes = SUB / 8 * B;
-
-  for (;;) {
-    if (tid == 0) s_tile = (long long)atomicAdd(&ctrl->ticket, 1u);
-    __syncthreads();
-    const long long gt = s_tile;
-    if (gt >= g.nsub) break;
+  unsigned short* my_idx = k3_idx + warp * K3_CHUNK;
+  const long long W = (long long)gridDim.x * K3_WARPS;
+  for (long long gt = (long long)blockIdx.x * K3_WARPS + warp; gt < g.nsub; gt += W) {
     const long long q = gt / g.spb, t = gt - q * g.spb;
     const long long j0 = q * g.epb + t * SUB;
     const long long bend = min((long long)g.n, (long long)((q + 1) * g.epb));
     const int cnt = (int)min((long long)SUB, bend - j0);
+    const T* pt = A.prev + j0;
+    const T* xt = A.cur + j0;
+    const unsigned short* ct = A.codes + j0;
+    unsigned short* halves = const_cast<unsigned short*>(A.codes) + j0;
+    unsigned char* tile_out = A.blob + g.off_index + q * g.block_stride + t * (long long)(SUB / 8 * B);
 
-    T pv[EPT], xv[EPT];
+    int count = 0;
+    unsigned my_ball = 0;      // lane l keeps the ballot of step (c0/32 + l) of the chunk
+    for (int c0 = 0; c0 < cnt; c0 += K3_CHUNK) {
+      const int ccnt = min(K3_CHUNK, cnt - c0);
+      for (int i0 = 0; i0 < K3_CHUNK / 32; i0 += K3_UNROLL) {
+        T pv[K3_UNROLL], xv[K3_UNROLL];
+        unsigned cv[K3_UNROLL];
 #pragma unroll
-    for (int k = 0; k < EPT; ++k) {
-      const int e = k * TILE_THREADS + tid;
-      pv[k] = (T)0;
-      xv[k] = (T)0;
-      if (e < cnt) {
-        pv[k] = ld_stream(A.prev + j0 + e);
-        xv[k] = ld_stream(A.cur + j0 + e);
-      }
-    }
-    unsigned ball[EPT];
-#pragma unroll
-    for (int k = 0; k < EPT; ++k) {
-      const int e = k * TILE_THREADS + tid;
-      unsigned idx = 0;
-      if (e < cnt)
-        idx = any ? Assigner<T>::run(pv[k], xv[k], c, rv, s_m, s_cf, A.mtab, A.cftab, M) : M;
-      s_idx[e] = (unsigned short)idx;
-      ball[k] = __ballot_sync(0xffffffffu, e < cnt && idx == M);
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int k = 0; k < EPT; ++k) s_chunk[k * (TILE_THREADS / 32) + warp] = __popc(ball[k]);
-    }
-    __syncthreads();
-    if (warp == 0) {
-      int v[NCHUNK / 32];
-      int sum = 0;
-#pragma unroll
-      for (int i = 0; i < NCHUNK / 32; ++i) { v[i] = s_chunk[lane * (NCHUNK / 32) + i]; sum += v[i]; }
-      const int incl = warp_incl_scan(sum);
-      int ex = incl - sum;
-#pragma unroll
-      for (int i = 0; i < NCHUNK / 32; ++i) { s_chunk[lane * (NCHUNK / 32) + i] = ex; ex += v[i]; }
-      const int total = __shfl_sync(0xffffffffu, incl, 31);
-      if (lane == 0) {
-        s_total = total;
-        s_P = lookback(A.tstatus, gt, total, blob_status);
-      }
-    }
-    __syncthreads();
-    const long long P = s_P;
-
-    // incompressible values, in element order (bit copies)
-#pragma unroll
-    for (int k = 0; k < EPT; ++k) {
-      if ((ball[k] >> lane) & 1u) {
-        const long long pos = P + s_chunk[k * (TILE_THREADS / 32) + warp] +
-                              __popc(ball[k] & lanemask_lt());
-        exact_u[pos] = Bits<T>::of(xv[k]);
-      }
-    }
-
-    // bit-pack the tile: index e occupies bits [e*B, e*B + B), least significant bit first
-    {
-      const int nbytes = (cnt * B + 7) >> 3;
-      const int nv16 = (nbytes + 15) >> 4;
-      uint4* out = reinterpret_cast<uint4*>(A.blob + g.off_index + q * g.block_stride +
-                                            t * (long long)tile_bytes);
-      for (int v = tid; v < nv16; v += TILE_THREADS) {
-        unsigned w[4];
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const int bit0 = (v * 4 + h) * 32;
-          int e = bit0 / B;
-          const int e_end = min((bit0 + 31) / B, SUB - 1);
-          unsigned long long acc = 0;
-          for (; e <= e_end; ++e) {
-            const int sh = e * B - bit0;
-            const unsigned long long x = s_idx[e];
-            acc |= sh >= 0 ? (x << sh) : (x >> (-sh));
+        for (int u = 0; u < K3_UNROLL; ++u) {
+          const int e = (i0 + u) * 32 + lane;
+          pv[u] = (T)0;
+          xv[u] = (T)0;
+          cv[u] = CODE_NONE;
+          if (e < ccnt) {
+            cv[u] = __ldcs(ct + c0 + e);
+            pv[u] = ld_stream(pt + c0 + e);
+            xv[u] = ld_stream(xt + c0 + e);
           }
-          w[h] = (unsigned)acc;
         }
-        out[v] = make_uint4(w[0], w[1], w[2], w[3]);
+#pragma unroll
+        for (int u = 0; u < K3_UNROLL; ++u) {
+          const int e = (i0 + u) * 32 + lane;
+          unsigned idx = 0;
+          if (e < ccnt)
+            idx = any ? Assigner<T>::run(pv[u], xv[u], cv[u], cbase, c, rv, s_m, s_cf, A.mtab,
+                                         A.cftab, M)
+                      : M;
+          my_idx[e] = (unsigned short)idx;
+          const unsigned ball = __ballot_sync(0xffffffffu, e < ccnt && idx == M);
+          if (lane == i0 + u) my_ball = ball;
+          count += __popc(ball);
+        }
       }
+      __syncwarp();
+      // the chunk's ballots, as 16-bit halves over the tile's consumed codes
+      {
+        const int s0 = (c0 >> 5) + lane;     // step of this lane's ballot
+        if (s0 * 32 < cnt) halves[2 * s0] = (unsigned short)(my_ball & 0xFFFFu);
+        if (s0 * 32 + 16 < cnt) halves[2 * s0 + 1] = (unsigned short)(my_ball >> 16);
+      }
+      // bit-pack the chunk: index e at bits [e*B, e*B + B) of the tile, LSB first; the image
+      // of the tile is padded with zero bytes to a multiple of 16
+      const int nwords = ((((ccnt * B + 7) >> 3) + 15) >> 4) * 4;
+      unsigned* out = reinterpret_cast<unsigned*>(tile_out + (long long)(c0 / 8) * B);
+      for (int w = lane; w < nwords; w += 32) {
+        const int bit0 = w * 32;
+        int e = bit0 / B;
+        const int e_end = min((bit0 + 31) / B, ccnt - 1);
+        unsigned long long acc = 0;
+        for (; e <= e_end; ++e) {
+          const int sh = e * B - bit0;
+          const unsigned long long xx = my_idx[e];
+          acc |= sh >= 0 ? (xx << sh) : (xx >> (-sh));
+        }
+        out[w] = (unsigned)acc;
+      }
+      __syncwarp();
     }
+    if (lane == 0) A.tstatus[gt] = (unsigned long long)count;
+  }
+}
 
-    if (tid == 0) {
-      sub_off[gt] = P;
-      if (t == 0) inc_off[q] = P;
-      if (gt == g.nsub - 1) {
-        const long long n_inc = P + s_total;
-        inc_off[g.nblocks] = n_inc;
-        numarck_header* h = reinterpret_cast<numarck_header*>(A.blob);
-        h->n_inc = n_inc;
-        h->total_bytes = g.off_exact + n_inc * (long long)sizeof(T);
+// K3b — the incompressible offsets (§IV.C): exclusive prefix of the per-tile counts gives the
+// sub-block table; its entries at block starts give the per-block table; the total is n_inc.
+// One CTA of 1024 threads; each thread scans a contiguous run of tiles.
+__global__ void __launch_bounds__(1024, 1) k3_scan(const unsigned long long* counts, Geometry g,
+                                                  unsigned char* blob, int L) {
+  __shared__ long long s_w[33];
+  const int tid = (int)threadIdx.x;
+  const long long per = (g.nsub + 1023) / 1024;
+  const long long lo = min((long long)g.nsub, tid * per), hi = min((long long)g.nsub, lo + per);
+  long long sum = 0;
+  for (long long i = lo; i < hi; ++i) sum += (long long)counts[i];
+  // block exclusive scan of the per-thread sums
+  const int lane = (int)lane_id(), w = tid >> 5;
+  long long inc = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  if (lane == 31) s_w[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const long long v = s_w[lane];
+    long long vi = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long u = __shfl_up_sync(0xffffffffu, vi, o);
+      if (lane >= o) vi += u;
+    }
+    s_w[lane] = vi - v;
+    if (lane == 31) s_w[32] = vi;
+  }
+  __syncthreads();
+  long long run = s_w[w] + inc - sum;
+  int64_t* sub_off = reinterpret_cast<int64_t*>(blob + g.off_sub_off);
+  int64_t* inc_off = reinterpret_cast<int64_t*>(blob + g.off_inc_off);
+  for (long long i = lo; i < hi; ++i) {
+    sub_off[i] = run;
+    if (i % g.spb == 0) inc_off[i / g.spb] = run;
+    run += (long long)counts[i];
+  }
+  if (tid == 0) {
+    const long long n_inc = s_w[32];
+    inc_off[g.nblocks] = n_inc;
+    numarck_header* h = reinterpret_cast<numarck_header*>(blob);
+    h->n_inc = n_inc;
+    h->total_bytes = g.off_exact + n_inc * (long long)L;
+  }
+}
+
+// K3c — incompressible values (§III.C): each warp takes a tile, reads all of its half-ballots
+// (before writing anything: the tile's own values may land on them) and its offset, then copies
+// the cur values of its incompressible points, in element order, into the incompressible table
+// (bit copies; only the sectors that hold those points are read).
+template <typename T>
+__global__ void __launch_bounds__(512) k3_exact(const T* __restrict__ cur,
+                                                const unsigned short* codes, Geometry g,
+                                                unsigned char* blob) {
+  using U = typename Bits<T>::U;
+  const int lane = (int)lane_id();
+  const long long W = (long long)gridDim.x * (blockDim.x >> 5);
+  U* exact_u = reinterpret_cast<U*>(blob + g.off_exact);
+  const int64_t* sub_off = reinterpret_cast<const int64_t*>(blob + g.off_sub_off);
+  const U* xu = reinterpret_cast<const U*>(cur);
+  for (long long gt = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); gt < g.nsub;
+       gt += W) {
+    const long long q = gt / g.spb, t = gt - q * g.spb;
+    const long long j0 = q * g.epb + t * SUB;
+    const long long bend = min((long long)g.n, (long long)((q + 1) * g.epb));
+    const int cnt = (int)min((long long)SUB, bend - j0);
+    const unsigned short* halves = codes + j0;
+    // lane l holds the ballots of steps l, l+32, l+64, l+96
+    unsigned mine[STEPS / 32];
+#pragma unroll
+    for (int k = 0; k < STEPS / 32; ++k) {
+      const int st = k * 32 + lane;
+      const unsigned lo = st * 32 < cnt ? halves[2 * st] : 0u;
+      const unsigned hi = st * 32 + 16 < cnt ? halves[2 * st + 1] : 0u;
+      mine[k] = lo | (hi << 16);
+    }
+    __syncwarp();
+    long long run = sub_off[gt];
+#pragma unroll
+    for (int k = 0; k < STEPS / 32; ++k) {
+      unsigned any = __ballot_sync(0xffffffffu, mine[k] != 0u);
+      while (any) {
+        const int s = __ffs(any) - 1;
+        any &= any - 1;
+        const unsigned ball = __shfl_sync(0xffffffffu, mine[k], s);
+        if ((ball >> lane) & 1u)
+          exact_u[run + __popc(ball & lanemask_lt())] = xu[j0 + (long long)(k * 32 + s) * 32 + lane];
+        run += __popc(ball);
       }
     }
-    __syncthreads();
   }
 }
 
@@ -296,6 +332,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 2) k3_assign(AssignArgs<T> A) {
 
 template <typename T>
 static cudaError_t launch_assign_t(const CompressPlan& P, cudaStream_t s, const Consts<T>& c) {
+  if (P.g.nsub == 0) return cudaSuccess;   // n == 0: K2 already wrote every table
   AssignArgs<T> A;
   A.prev = static_cast<const T*>(P.prev);
   A.cur = static_cast<const T*>(P.cur);
@@ -307,21 +344,44 @@ static cudaError_t launch_assign_t(const CompressPlan& P, cudaStream_t s, const 
   A.cftab = reinterpret_cast<const float*>(P.ws + P.wl.cftab);
   A.tstatus = reinterpret_cast<unsigned long long*>(P.ws + P.wl.status);
   A.blob = P.blob;
+  A.codes = reinterpret_cast<const unsigned short*>(P.blob + code_offset(P.g));
   static int occ[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
   int per_sm = dev < 64 ? occ[dev] : 0;
+  const int dyn = K3_WARPS * K3_WARP_SMEM;
   if (per_sm == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_assign<T>,
-                                                                  TILE_THREADS, 0);
+    cudaError_t e = cudaFuncSetAttribute(k3_assign<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         dyn);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_assign<T>, K3_THREADS, dyn);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     if (dev < 64) occ[dev] = per_sm;
   }
   long long blocks = (long long)P.sms * per_sm;
-  if (blocks > P.g.nsub) blocks = P.g.nsub;
-  if (blocks < 1) return cudaSuccess;   // n == 0: K2 already wrote every table
-  k3_assign<T><<<(int)blocks, TILE_THREADS, 0, s>>>(A);
+  const long long need = (P.g.nsub + K3_WARPS - 1) / K3_WARPS;
+  if (blocks > need) blocks = need;
+  k3_assign<T><<<(int)blocks, K3_THREADS, dyn, s>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_offsets(const CompressPlan& P, cudaStream_t s) {
+  if (P.g.nsub == 0) return cudaSuccess;
+  k3_scan<<<1, 1024, 0, s>>>(reinterpret_cast<const unsigned long long*>(P.ws + P.wl.status), P.g,
+                             P.blob, P.g.dtype == NUMARCK_F64 ? 8 : 4);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_exact(const CompressPlan& P, cudaStream_t s) {
+  if (P.g.nsub == 0) return cudaSuccess;
+  long long xb = (P.g.nsub + 15) / 16;
+  if (xb > (long long)P.sms * 4) xb = (long long)P.sms * 4;
+  const unsigned short* codes = reinterpret_cast<const unsigned short*>(P.blob + code_offset(P.g));
+  if (P.g.dtype == NUMARCK_F64)
+    k3_exact<double><<<(int)xb, 512, 0, s>>>(static_cast<const double*>(P.cur), codes, P.g, P.blob);
+  else
+    k3_exact<float><<<(int)xb, 512, 0, s>>>(static_cast<const float*>(P.cur), codes, P.g, P.blob);
   return cudaGetLastError();
 }
 

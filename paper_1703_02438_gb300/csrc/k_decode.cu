@@ -38,20 +38,21 @@ struct BitsOf<double> {
   using U = unsigned long long;
 };
 
-constexpr int WORDS = SUB * NUMARCK_MAX_B / 32 + 8;
+constexpr int K4_WARPS = 16;                    // warps per CTA (each owns whole tiles)
+constexpr int K4_THREADS = K4_WARPS * 32;
+constexpr int K4_CHUNK = 1024;                  // elements decoded per step of a warp
+constexpr int K4_UNROLL = 8;                    // 32-element steps whose loads are in flight
+constexpr int K4_WORDS = K4_CHUNK * NUMARCK_MAX_B / 32 + 8;   // packed words of a chunk (+guard)
+constexpr int K4_DYN_SMEM = DM_SMEM * 8 + K4_WARPS * K4_WORDS * 4;
 
-struct DecodeShared {
-  __align__(16) unsigned char mraw[DM_SMEM * 8];   // multipliers m = 1 + centre (T)
-  __align__(16) unsigned words[WORDS];              // packed index bits of one tile
-  int chunk[NCHUNK];
-  int total;
-  int bad;
-};
-
+// One warp decodes one 4096-element tile at a time, in 1024-element chunks: it copies the
+// chunk's packed bits into its shared buffer, unpacks B-bit fields, and walks the chunk in
+// 32-element steps, numbering incompressible points with ballots from the tile's entry in the
+// sub-block offset table. No block-wide barrier is needed after the multiplier table is built.
 template <typename T>
 __device__ __forceinline__ void decode_tiles(const DecodeArgs& A, const Geometry& g,
                                              long long n_inc, long long g0, long long g1,
-                                             DecodeShared& S) {
+                                             unsigned char* dyn) {
   const int tid = (int)threadIdx.x;
   const int lane = (int)lane_id();
   const int warp = tid >> 5;
@@ -67,103 +68,92 @@ __device__ __forceinline__ void decode_tiles(const DecodeArgs& A, const Geometry
   const T* prev = static_cast<const T*>(A.prev_seg);
   T* out = static_cast<T*>(A.out_seg);
   U* out_u = reinterpret_cast<U*>(A.out_seg);
-  T* s_m = reinterpret_cast<T*>(S.mraw);
+  T* s_m = reinterpret_cast<T*>(dyn);
+  unsigned* words = reinterpret_cast<unsigned*>(dyn + DM_SMEM * 8) + warp * K4_WORDS;
 
   const int nm = min(1 << B, DM_SMEM);
-  for (int r = tid; r < nm; r += TILE_THREADS) s_m[r] = t_add((T)1, centres[r]);
+  for (int r = tid; r < nm; r += K4_THREADS) s_m[r] = t_add((T)1, centres[r]);
+  __syncthreads();   // the only block-wide barrier
 
   const long long seg_lo = A.start, seg_hi = A.start + A.count;
-  const int tile_bytes = SUB / 8 * B;
-  for (long long gt = g0 + blockIdx.x; gt <= g1; gt += gridDim.x) {
+  const long long W = (long long)gridDim.x * K4_WARPS;
+  for (long long gt = g0 + (long long)blockIdx.x * K4_WARPS + warp; gt <= g1; gt += W) {
     const long long q = gt / g.spb, t = gt - q * g.spb;
     const long long j0 = q * g.epb + t * SUB;
     const long long bend = min((long long)g.n, (long long)((q + 1) * g.epb));
     const int cnt = (int)min((long long)SUB, bend - j0);
     const long long base = sub_off[gt];
     const long long boff = idx_off[q];
-    const int nbytes = (cnt * B + 7) >> 3;
-    const int nv16 = (nbytes + 15) >> 4;
-    const long long tstart = boff + t * (long long)tile_bytes;
-    __syncthreads();   // the previous tile is done with S.words / S.chunk
-    if (tid == 0)
-      S.bad = (base < 0 || base > n_inc || (boff & 15) || boff < 0 ||
-               tstart + 16LL * nv16 > g.index_bytes) ? 1 : 0;
-    __syncthreads();
-    if (S.bad) {
-      if (tid == 0 && A.status) atomicExch(A.status, NUMARCK_ERR_CORRUPT);
+    const long long tstart = boff + t * (long long)(SUB / 8 * B);
+    const long long tend = tstart + 16LL * (((cnt * B + 7) / 8 + 15) / 16);
+    if (base < 0 || base > n_inc || (boff & 15) || boff < 0 || tend > g.index_bytes) {
+      if (lane == 0 && A.status) atomicExch(A.status, NUMARCK_ERR_CORRUPT);
       continue;
     }
-    const uint4* src = reinterpret_cast<const uint4*>(index + tstart);
-    for (int v = tid; v < nv16; v += TILE_THREADS)
-      reinterpret_cast<uint4*>(S.words)[v] = __ldcs(src + v);
-    if (tid < 8) S.words[nv16 * 4 + tid] = 0u;
-    __syncthreads();
-
-    unsigned idx[EPT], ball[EPT];
+    long long run = base;
+    bool whole = true;
+    for (int c0 = 0; c0 < cnt; c0 += K4_CHUNK) {
+      const long long cj = j0 + c0;
+      if (cj >= seg_hi) { whole = false; break; }
+      const int ccnt = min(K4_CHUNK, cnt - c0);
+      const int nv16 = (((ccnt * B + 7) >> 3) + 15) >> 4;
+      const uint4* src = reinterpret_cast<const uint4*>(index + tstart + (c0 / 8) * B);
+      for (int v = lane; v < nv16; v += 32) reinterpret_cast<uint4*>(words)[v] = __ldcs(src + v);
+      if (lane < 4) words[nv16 * 4 + lane] = 0u;
+      __syncwarp();
+      const bool emit = cj + ccnt > seg_lo;   // else: only count this chunk's markers
+      for (int i0 = 0; i0 < K4_CHUNK / 32; i0 += K4_UNROLL) {
+        T pv[K4_UNROLL];
 #pragma unroll
-    for (int k = 0; k < EPT; ++k) {
-      const int e = k * TILE_THREADS + tid;
-      unsigned id = 0;
-      if (e < cnt) {
-        const unsigned bp = (unsigned)e * (unsigned)B;
-        const unsigned w = bp >> 5, o = bp & 31u;
-        const unsigned long long v2 =
-            ((unsigned long long)S.words[w + 1] << 32) | (unsigned long long)S.words[w];
-        id = (unsigned)(v2 >> o) & mask;
-      }
-      idx[k] = id;
-      ball[k] = __ballot_sync(0xffffffffu, e < cnt && id == M);
-    }
-    if (lane == 0) {
+        for (int u = 0; u < K4_UNROLL; ++u) {
+          const int e = (i0 + u) * 32 + lane;
+          const long long j = cj + e;
+          pv[u] = (emit && e < ccnt && j >= seg_lo && j < seg_hi) ? ld_stream(prev + (j - seg_lo))
+                                                                   : (T)0;
+        }
 #pragma unroll
-      for (int k = 0; k < EPT; ++k) S.chunk[k * (TILE_THREADS / 32) + warp] = __popc(ball[k]);
-    }
-    __syncthreads();
-    if (warp == 0) {
-      int v[NCHUNK / 32];
-      int sum = 0;
-#pragma unroll
-      for (int i = 0; i < NCHUNK / 32; ++i) { v[i] = S.chunk[lane * (NCHUNK / 32) + i]; sum += v[i]; }
-      const int incl = warp_incl_scan(sum);
-      int ex = incl - sum;
-#pragma unroll
-      for (int i = 0; i < NCHUNK / 32; ++i) { S.chunk[lane * (NCHUNK / 32) + i] = ex; ex += v[i]; }
-      if (lane == 31) S.total = incl;
-    }
-    __syncthreads();
-    if (tid == 0 && A.status) {
-      const long long next = (gt + 1 < g.nsub) ? sub_off[gt + 1] : n_inc;
-      if (base + S.total != next) atomicExch(A.status, NUMARCK_ERR_CORRUPT);
-    }
-
-#pragma unroll
-    for (int k = 0; k < EPT; ++k) {
-      const int e = k * TILE_THREADS + tid;
-      const long long j = j0 + e;
-      if (e < cnt && j >= seg_lo && j < seg_hi) {
-        const long long o = j - seg_lo;
-        if ((ball[k] >> lane) & 1u) {
-          const long long pos =
-              base + S.chunk[k * (TILE_THREADS / 32) + warp] + __popc(ball[k] & lanemask_lt());
-          if (pos < n_inc) {
-            out_u[o] = exact_u[pos];
-          } else {
-            out_u[o] = 0;
-            if (A.status) atomicExch(A.status, NUMARCK_ERR_CORRUPT);
+        for (int u = 0; u < K4_UNROLL; ++u) {
+          const int e = (i0 + u) * 32 + lane;
+          unsigned id = 0;
+          if (e < ccnt) {
+            const unsigned bp = (unsigned)e * (unsigned)B;
+            const unsigned w = bp >> 5, o = bp & 31u;
+            const unsigned long long v2 =
+                ((unsigned long long)words[w + 1] << 32) | (unsigned long long)words[w];
+            id = (unsigned)(v2 >> o) & mask;
           }
-        } else {
-          const T p = ld_stream(prev + o);
-          const unsigned r = idx[k];
-          const T m = r < (unsigned)DM_SMEM ? s_m[r] : t_add((T)1, centres[r]);
-          out[o] = t_mul(p, m);
+          const bool mk = e < ccnt && id == M;
+          const unsigned ball = __ballot_sync(0xffffffffu, mk);
+          const long long j = cj + e;
+          if (emit && e < ccnt && j >= seg_lo && j < seg_hi) {
+            const long long o = j - seg_lo;
+            if (mk) {
+              const long long pos = run + __popc(ball & lanemask_lt());
+              if (pos < n_inc) {
+                out_u[o] = exact_u[pos];
+              } else {
+                out_u[o] = 0;
+                if (A.status) atomicExch(A.status, NUMARCK_ERR_CORRUPT);
+              }
+            } else {
+              const T m = id < (unsigned)DM_SMEM ? s_m[id] : t_add((T)1, centres[id]);
+              out[o] = t_mul(pv[u], m);
+            }
+          }
+          run += __popc(ball);
         }
       }
+      __syncwarp();
+    }
+    if (whole && lane == 0 && A.status) {
+      const long long next = (gt + 1 < g.nsub) ? sub_off[gt + 1] : n_inc;
+      if (run != next) atomicExch(A.status, NUMARCK_ERR_CORRUPT);
     }
   }
 }
 
-__global__ void __launch_bounds__(TILE_THREADS, 2) k4_decode(DecodeArgs A) {
-  __shared__ DecodeShared S;
+__global__ void __launch_bounds__(K4_THREADS, 2) k4_decode(DecodeArgs A) {
+  extern __shared__ __align__(16) unsigned char k4_dyn[];
   __shared__ __align__(16) numarck_header s_h;
   __shared__ Geometry s_g;
   __shared__ long long s_g0, s_g1;
@@ -187,7 +177,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 2) k4_decode(DecodeArgs A) {
       g1 = q1 * g.spb + (last - q1 * g.epb) / SUB;
     }
     if (rc && blockIdx.x == 0 && A.status) atomicExch(A.status, rc);
-    s_ok = rc == 0 && g1 >= g0 + (long long)blockIdx.x;
+    s_ok = rc == 0 && g1 >= g0 + (long long)blockIdx.x * K4_WARPS;
     s_g = g;
     s_g0 = g0;
     s_g1 = g1;
@@ -196,9 +186,9 @@ __global__ void __launch_bounds__(TILE_THREADS, 2) k4_decode(DecodeArgs A) {
   if (!s_ok) return;
   const Geometry g = s_g;
   if (g.dtype == NUMARCK_F64)
-    decode_tiles<double>(A, g, s_h.n_inc, s_g0, s_g1, S);
+    decode_tiles<double>(A, g, s_h.n_inc, s_g0, s_g1, k4_dyn);
   else
-    decode_tiles<float>(A, g, s_h.n_inc, s_g0, s_g1, S);
+    decode_tiles<float>(A, g, s_h.n_inc, s_g0, s_g1, k4_dyn);
 }
 
 }  // namespace
@@ -210,16 +200,21 @@ cudaError_t launch_decode(const DecodePlan& P, cudaStream_t s) {
   cudaGetDevice(&dev);
   int per_sm = dev < 64 ? occ[dev] : 0;
   if (per_sm == 0) {
-    cudaError_t e =
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k4_decode, TILE_THREADS, 0);
+    cudaError_t e = cudaFuncSetAttribute(k4_decode, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         K4_DYN_SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k4_decode, K4_THREADS, K4_DYN_SMEM);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     if (dev < 64) occ[dev] = per_sm;
   }
   long long blocks = (long long)P.sms * per_sm;
-  if (P.ntiles_hint > 0 && blocks > P.ntiles_hint) blocks = P.ntiles_hint;
+  if (P.ntiles_hint > 0) {
+    const long long need = (P.ntiles_hint + K4_WARPS - 1) / K4_WARPS;
+    if (blocks > need) blocks = need;
+  }
   DecodeArgs A{P.blob, P.prev_seg, P.out_seg, P.status, P.start, P.count, P.n_expected};
-  k4_decode<<<(int)blocks, TILE_THREADS, 0, s>>>(A);
+  k4_decode<<<(int)blocks, K4_THREADS, K4_DYN_SMEM, s>>>(A);
   return cudaGetLastError();
 }
 

@@ -20,7 +20,7 @@ __device__ __forceinline__ void anchor_min_consts(Consts<T>& c, const Ctrl* ctrl
   if (a == 0.0) a = 0.0;  // a zero minimum is taken as +0
   c.a = (T)a;             // exact: the key was made from a T value
   c.af = (float)c.a;
-  c.K0 = __fadd_ru(__fmul_ru(__fmul_ru(0x1p-22f, c.inv_wf), fabsf(c.af)), 0x1p-100f);
+  c.K0 = __fadd_ru(__fmul_ru(__fmul_ru(0x1p-18f, c.inv_wf), fabsf(c.af)), 0x1p-60f);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -58,7 +58,15 @@ struct HistCtx {
   Ctrl* ctrl;
   int sbase;
   int hbase;
+  int cbase;                  // bin of code 0
+  unsigned short* codes;      // per-element bin codes (scratch at the blob's tail)
 };
+
+__device__ __forceinline__ unsigned short bin_code(const HistCtx& h, bool binned, int b) {
+  if (!binned) return (unsigned short)CODE_NONE;
+  const unsigned off = (unsigned)(b - h.cbase);
+  return (unsigned short)(off < CODE_FAR ? off : CODE_FAR);
+}
 
 // All 32 lanes call this together (valid may differ per lane).
 __device__ __forceinline__ void hist_add(const HistCtx& h, bool valid, int b) {
@@ -91,8 +99,7 @@ struct Classifier<float> {
 template <>
 struct Classifier<double> {
   __device__ __forceinline__ static int run(double p, double x, const Consts<double>& c, int& b) {
-    Est e;
-    return classify_f64(p, x, c, b, e);
+    return classify_f64(p, x, c, b);
   }
 };
 
@@ -123,7 +130,8 @@ __global__ void __launch_bounds__(K1_THREADS) k1_hist(const T* __restrict__ prev
                                                       const T* __restrict__ cur, int64_t n,
                                                       Consts<T> c, int anchor_min, Ctrl* ctrl,
                                                       unsigned long long* hist,
-                                                      unsigned long long* tstatus, int64_t nsub) {
+                                                      unsigned long long* tstatus, int64_t nsub,
+                                                      unsigned short* codes) {
   extern __shared__ unsigned int sh[];
   if (anchor_min) anchor_min_consts<T>(c, ctrl);
   int c0 = 0;  // bin of a zero change ratio: centre of the shared window
@@ -131,7 +139,8 @@ __global__ void __launch_bounds__(K1_THREADS) k1_hist(const T* __restrict__ prev
     const double z = floor(-(double)c.a * (double)c.inv_w);
     c0 = (int)fmin(fmax(z, 0.0), (double)(1 << (WIN_LOG2 + 1)));
   }
-  HistCtx h{sh, hist, ctrl, c0 - SH_BINS / 2, c.hbase};
+  HistCtx h{sh, hist, ctrl, c0 - SH_BINS / 2, c.hbase, c0 - CODE_HALF, codes};
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->code_base = h.cbase;
 
   for (int i = threadIdx.x; i < SH_BINS; i += blockDim.x) sh[i] = 0u;
   // K3's scan state and tile counter for this call
@@ -166,11 +175,13 @@ __global__ void __launch_bounds__(K1_THREADS) k1_hist(const T* __restrict__ prev
       }
 #pragma unroll
       for (int u = 0; u < K1_UNROLL; ++u) {
+        const int64_t vi = base + u * 32 + lane;
 #pragma unroll
         for (int v = 0; v < V::N; ++v) {
           int b = 0;
           const bool binned = ok[u] && Classifier<T>::run(pe[u][v], xe[u][v], c, b);
           if (binned) { lmin = min(lmin, b); lmax = max(lmax, b); }
+          if (ok[u]) codes[vi * V::N + v] = bin_code(h, binned, b);
           hist_add(h, binned, b);
         }
       }
@@ -183,6 +194,7 @@ __global__ void __launch_bounds__(K1_THREADS) k1_hist(const T* __restrict__ prev
       bool binned = false;
       if (j < n) binned = Classifier<T>::run(ld_stream(prev + j), ld_stream(cur + j), c, b);
       if (binned) { lmin = min(lmin, b); lmax = max(lmax, b); }
+      if (j < n) codes[j] = bin_code(h, binned, b);
       hist_add(h, binned, b);
     }
   } else {
@@ -202,6 +214,7 @@ __global__ void __launch_bounds__(K1_THREADS) k1_hist(const T* __restrict__ prev
         int b = 0;
         const bool binned = ok[u] && Classifier<T>::run(pe[u], xe[u], c, b);
         if (binned) { lmin = min(lmin, b); lmax = max(lmax, b); }
+        if (ok[u]) codes[base + u * 32 + lane] = bin_code(h, binned, b);
         hist_add(h, binned, b);
       }
     }
@@ -258,25 +271,30 @@ cudaError_t launch_anchor_min_t(const CompressPlan& P, cudaStream_t s) {
 
 template <typename T, bool VEC>
 cudaError_t launch_hist_tv(const CompressPlan& P, cudaStream_t s) {
-  static thread_local int configured_dev = -1;
+  static int occ[64] = {0};   // resident CTAs per SM, per device (0 = not configured yet)
   int dev = 0;
   cudaGetDevice(&dev);
   const size_t smem = SH_BINS * sizeof(unsigned int);
-  if (configured_dev != dev) {
+  int per_sm = dev < 64 ? occ[dev] : 0;
+  if (per_sm == 0) {
     cudaError_t e = cudaFuncSetAttribute(k1_hist<T, VEC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    configured_dev = dev;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k1_hist<T, VEC>, K1_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (dev < 64) occ[dev] = per_sm;
   }
   Ctrl* ctrl = reinterpret_cast<Ctrl*>(P.ws + P.wl.ctrl);
   auto* hist = reinterpret_cast<unsigned long long*>(P.ws + P.wl.hist);
   auto* tstat = reinterpret_cast<unsigned long long*>(P.ws + P.wl.status);
-  // 3 CTAs of 512 threads per SM (64 KB shared window each); enough elements per CTA that the
-  // window set-up and merge stay small next to the streaming work.
-  const int blocks = grid_for(P.g.n, K1_THREADS * 32, P.sms * 3);
+  // one wave of resident CTAs; small inputs use fewer CTAs so that the shared-window set-up and
+  // merge stay small next to the streaming work (at least 32 elements per thread)
+  const int blocks = grid_for(P.g.n, K1_THREADS * 32, P.sms * per_sm);
   k1_hist<T, VEC><<<blocks, K1_THREADS, smem, s>>>(
       static_cast<const T*>(P.prev), static_cast<const T*>(P.cur), P.g.n, consts_of<T>(P),
-      P.g.anchor == NUMARCK_ANCHOR_MIN ? 1 : 0, ctrl, hist, tstat, P.g.nsub);
+      P.g.anchor == NUMARCK_ANCHOR_MIN ? 1 : 0, ctrl, hist, tstat, P.g.nsub,
+      reinterpret_cast<unsigned short*>(P.blob + code_offset(P.g)));
   return cudaGetLastError();
 }
 

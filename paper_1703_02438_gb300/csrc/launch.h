@@ -36,7 +36,9 @@ struct DecodePlan {
 cudaError_t launch_anchor_min(const CompressPlan& P, cudaStream_t s);  // K0 (ANCHOR_MIN only)
 cudaError_t launch_hist(const CompressPlan& P, cudaStream_t s);        // K1
 cudaError_t launch_topk(const CompressPlan& P, cudaStream_t s);        // K2
-cudaError_t launch_assign(const CompressPlan& P, cudaStream_t s);      // K3
+cudaError_t launch_assign(const CompressPlan& P, cudaStream_t s);      // K3a: indices + packing
+cudaError_t launch_offsets(const CompressPlan& P, cudaStream_t s);     // K3b: offset tables
+cudaError_t launch_exact(const CompressPlan& P, cudaStream_t s);       // K3c: incompressible values
 cudaError_t launch_decode(const DecodePlan& P, cudaStream_t s);        // K4 / K5
 
 }  // namespace nmk
