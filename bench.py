@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 24,
                     help="elements of the oracle's bounded sample")
+    ap.add_argument("--workload", default="flash", choices=["flash", "batched"],
+                    help="flash: the headline 1024^3 series; batched: 256 mixed variables, "
+                         "per-variable launches vs one graph-captured batch")
+    ap.add_argument("--batch-count", type=int, default=256)
     return ap.parse_args()
 
 
@@ -219,10 +223,95 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------------------
+def run_batched(args):
+    """256 variables (sizes log-uniform in [1e4, 2e8], float32/float64, per-variable E and B):
+    per-variable launches on one stream vs one autotuned batch captured in a CUDA graph."""
+    import torch
+    from paper_1703_02438_gb300 import autotune
+    from paper_1703_02438_gb300 import build as nbuild
+    from paper_1703_02438_gb300 import numarck as N
+    from paper_1703_02438_gb300 import synth
+    nbuild.build()
+    dev = torch.device("cuda", 0)
+    specs = synth.batch_specs(count=args.batch_count)
+    pairs = []
+    for i, (n, dtype, E, B, scale) in enumerate(specs):
+        pairs.append(synth.plain_pair(n, dtype=dtype, seed=synth.seed_for(3, 1000 + i),
+                                      scale=scale, device=dev))
+    torch.cuda.synchronize()
+    nbytes = sum(p.numel() * p.element_size() for p, _ in pairs)
+    batch = N.Batch(pairs, [(E, B) for _, _, E, B, _ in specs])
+    prevs = [p for p, _ in pairs]
+    outs = [torch.empty_like(p) for p in prevs]
+    ws = N.Workspace(dev)
+    stream = torch.cuda.current_stream()
+
+    def plain_compress():
+        for (p, x), (_, _, E, B, _), blob in zip(pairs, specs, batch.blobs):
+            N.compress(p, x, E, B, blob=blob, workspace=ws)
+
+    def plain_decompress():
+        for p, blob, o in zip(prevs, batch.blobs, outs):
+            N.decompress(blob, p, out=o)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    reps = max(1, args.steps)
+    for _ in range(args.warmup):
+        plain_compress()
+        plain_decompress()
+    t_pc = timed(plain_compress, reps)
+    t_pd = timed(plain_decompress, reps)
+    lanes, share, tune_ms = autotune.tune(batch, reps=1, use_cache=False)
+    batch.run()
+    N.decompress_batch(batch.blobs, prevs, outs=outs, lanes=lanes, grid_share=share)
+    torch.cuda.synchronize()
+    gc, gd = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    cs = torch.cuda.Stream()
+    cs.wait_stream(stream)
+    with torch.cuda.stream(cs):
+        with torch.cuda.graph(gc, stream=cs):
+            batch.run()
+        with torch.cuda.graph(gd, stream=cs):
+            N.decompress_batch(batch.blobs, prevs, outs=outs, lanes=lanes, grid_share=share)
+    torch.cuda.synchronize()
+    t_bc = timed(gc.replay, reps)
+    t_bd = timed(gd.replay, reps)
+    sizes = [n for n, *_ in specs]
+    line = {"metric": "batched compress+decompress input GB/s (graph-captured batch vs "
+                      "per-variable launches)",
+            "value": nbytes / ((t_bc + t_bd) / 1e3) / 1e9, "unit": "GB/s", "n_gpus": 1,
+            "steps": reps, "warmup": args.warmup, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": f"{len(specs)} variables, n log-uniform [1e4, 2e8] "
+                                   f"(total {sum(sizes)} elements, {nbytes / 1e9:.1f} GB), "
+                                   "float32/float64 50/50, E in {1e-2,1e-3,1e-4}, B in {6,8,10}",
+                       "lanes": lanes, "grid_share": share},
+            "batched": {"compress_ms": t_bc, "decompress_ms": t_bd,
+                        "compress_gbs": nbytes / (t_bc / 1e3) / 1e9,
+                        "decompress_gbs": nbytes / (t_bd / 1e3) / 1e9},
+            "per_variable": {"compress_ms": t_pc, "decompress_ms": t_pd,
+                             "value": nbytes / ((t_pc + t_pd) / 1e3) / 1e9,
+                             "compress_gbs": nbytes / (t_pc / 1e3) / 1e9,
+                             "decompress_gbs": nbytes / (t_pd / 1e3) / 1e9},
+            "speedup": (t_pc + t_pd) / (t_bc + t_bd), "autotune_ms": tune_ms}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     rank, world = _rank_world()
     import numpy as np
     import torch

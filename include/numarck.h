@@ -276,6 +276,49 @@ int numarck_decompress_range(const void* blob, const void* header_host,
                              const void* prev_seg, int64_t start, int64_t count,
                              void* out_seg, int32_t* status_dev, numarck_stream_t stream);
 
+/* ---- batches of variables ----
+ * The paper stores several compressed variables in one file (§IV.D); a checkpoint holds many
+ * variables of different sizes, types, error bounds and index widths. A batch call compresses
+ * (or decompresses) all of them with the kernels of `lanes` variables in flight at once:
+ * variables are assigned to lanes longest-first, each lane is a stream of the library forked from
+ * `stream` with an event and joined back into it before the call's work completes, and kernel
+ * grids are sized for 1/grid_share of the GPU. The results are those of the single-variable
+ * entry points, byte for byte. The fork/join consists of event records and waits only, so a batch
+ * can be captured into a CUDA graph (make one uncaptured call per device first: it creates the
+ * library's lane streams and configures its kernels). Calls of different host threads are
+ * serialised inside the library while they are queued. */
+typedef struct numarck_batch_item {
+  const void* prev;        /* device array of n elements of params.dtype                    */
+  const void* cur;         /* device array of n elements of params.dtype                    */
+  int64_t n;
+  numarck_params params;   /* per-variable dtype, B, E, anchor and block size               */
+  void* blob;              /* device buffer, 256-byte aligned                               */
+  size_t blob_cap;         /* >= numarck_compress_bound(n, &params)                         */
+} numarck_batch_item;
+
+typedef struct numarck_batch_decode_item {
+  const void* blob;        /* device pointer to a complete blob (256-byte aligned)          */
+  const void* prev;        /* device array of n elements (the prev of the compression)     */
+  void* out;               /* device array of n elements; receives the reconstruction      */
+  int64_t n;               /* must equal the blob's n                                       */
+} numarck_batch_decode_item;
+
+/* Workspace bytes for numarck_compress_batch with this item list and lane count (one slice per
+ * lane, each the largest single-variable workspace of its lane). 0 if an item is invalid. */
+size_t numarck_batch_workspace_bytes(const numarck_batch_item* items, int count, int lanes);
+
+/* Compresses count variables. ws: device workspace of >= numarck_batch_workspace_bytes bytes,
+ * zero-filled before first use (numarck_workspace_init) and reusable. lanes >= 1 (clamped to
+ * count and 64), grid_share >= 1. Every item is validated on the host before any launch; the
+ * return value is the first item error found (nothing is queued then), else NUMARCK_OK. */
+int numarck_compress_batch(const numarck_batch_item* items, int count, int lanes, int grid_share,
+                           void* ws, size_t ws_bytes, numarck_stream_t stream);
+
+/* Decompresses count blobs (Eq. 4) with `lanes` in flight; status_dev as in
+ * numarck_decompress (shared by all items; may be NULL). */
+int numarck_decompress_batch(const numarck_batch_decode_item* items, int count, int lanes,
+                             int grid_share, int32_t* status_dev, numarck_stream_t stream);
+
 /* ---- tracing (kernel-level timing for profilers and benchmarks) ----
  * events : an array of `count` cudaEvent_t handles owned by the caller, or NULL to stop.
  * While set, every numarck_compress call made on this host thread records, on its stream,

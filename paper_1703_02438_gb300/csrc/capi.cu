@@ -59,8 +59,8 @@ WsLayout make_ws(const Geometry& g) {
   o += (size_t)65536 * 4;
   w.selb = o;
   o += (size_t)65536 * 4;
-  w.status = o;
-  o = (size_t)round_up((int64_t)(o + (size_t)g.nsub * 8), 256);
+  w.status = o;   // per-tile incompressible counts, then the offset scan's look-back flags
+  o = (size_t)round_up((int64_t)(o + (size_t)(g.nsub + g.nsub / 4096 + 2) * 8), 256);
   w.total = o;
   return w;
 }
@@ -171,9 +171,13 @@ int numarck_workspace_init(void* ws, size_t ws_bytes, numarck_stream_t stream) {
   return NUMARCK_OK;
 }
 
-int numarck_compress(const void* prev, const void* cur, int64_t n, const numarck_params* p,
-                     void* blob, size_t blob_cap, void* ws, size_t ws_bytes,
-                     numarck_stream_t stream) {
+}  // extern "C"
+
+namespace nmk {
+
+// Validates the arguments of one compression and fills its launch plan (no device access).
+int plan_compress(const void* prev, const void* cur, int64_t n, const numarck_params* p,
+                  void* blob, size_t blob_cap, void* ws, size_t ws_bytes, CompressPlan* out) {
   int rc = check_params(p);
   if (rc) return rc;
   if (n < 0 || n > MAX_N) return NUMARCK_ERR_INVALID_ARG;
@@ -187,7 +191,8 @@ int numarck_compress(const void* prev, const void* cur, int64_t n, const numarck
   if (blob_cap < (size_t)(g.off_exact + n * (int64_t)L)) return NUMARCK_ERR_CAPACITY;
   if (ws_bytes < wl.total) return NUMARCK_ERR_CAPACITY;
 
-  CompressPlan P{};
+  CompressPlan& P = *out;
+  P = CompressPlan{};
   P.prev = prev;
   P.cur = cur;
   P.blob = static_cast<unsigned char*>(blob);
@@ -195,8 +200,6 @@ int numarck_compress(const void* prev, const void* cur, int64_t n, const numarck
   P.wl = wl;
   P.g = g;
   P.aligned16 = aligned(prev, 16) && aligned(cur, 16);
-  P.sms = device_sms();
-  if (P.sms <= 0) return NUMARCK_ERR_CUDA;
   if (p->dtype == NUMARCK_F64)
     P.cd = make_consts<double>(p->E, p->anchor);
   else
@@ -225,10 +228,13 @@ int numarck_compress(const void* prev, const void* cur, int64_t n, const numarck
   h.off_index = g.off_index;
   h.off_exact = g.off_exact;
   h.total_bytes = g.off_exact;
+  return NUMARCK_OK;
+}
 
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+// Queues the kernels of a planned compression on stream s (P.sms must be set).
+int launch_compress(const CompressPlan& P, cudaStream_t s) {
   trace(0, 6, s);
-  if (p->anchor == NUMARCK_ANCHOR_MIN && launch_anchor_min(P, s) != cudaSuccess)
+  if (P.g.anchor == NUMARCK_ANCHOR_MIN && launch_anchor_min(P, s) != cudaSuccess)
     return NUMARCK_ERR_CUDA;
   if (launch_hist(P, s) != cudaSuccess) return NUMARCK_ERR_CUDA;
   trace(1, 6, s);
@@ -241,6 +247,48 @@ int numarck_compress(const void* prev, const void* cur, int64_t n, const numarck
   if (launch_exact(P, s) != cudaSuccess) return NUMARCK_ERR_CUDA;
   trace(5, 6, s);
   return NUMARCK_OK;
+}
+
+int current_device_sms() { return device_sms(); }
+
+int plan_decompress_check(const void* blob, const void* prev, void* out, int64_t n) {
+  if (!blob || !aligned(blob, 256) || n < 0) return NUMARCK_ERR_INVALID_ARG;
+  if (n > 0 && (!prev || !out || !aligned(prev, 4) || !aligned(out, 4))) return NUMARCK_ERR_INVALID_ARG;
+  return NUMARCK_OK;
+}
+
+int launch_decompress(const void* blob, const void* prev, void* out, int64_t n, int32_t* status,
+                      int sms, cudaStream_t s) {
+  if (n == 0) return NUMARCK_OK;
+  DecodePlan P{};
+  P.blob = static_cast<const unsigned char*>(blob);
+  P.prev_seg = prev;
+  P.out_seg = out;
+  P.status = status;
+  P.start = 0;
+  P.count = n;
+  P.n_expected = n;
+  P.ntiles_hint = 0;
+  P.sms = sms;
+  trace(0, 2, s);
+  if (launch_decode(P, s) != cudaSuccess) return NUMARCK_ERR_CUDA;
+  trace(1, 2, s);
+  return NUMARCK_OK;
+}
+
+}  // namespace nmk
+
+extern "C" {
+
+int numarck_compress(const void* prev, const void* cur, int64_t n, const numarck_params* p,
+                     void* blob, size_t blob_cap, void* ws, size_t ws_bytes,
+                     numarck_stream_t stream) {
+  CompressPlan P;
+  const int rc = plan_compress(prev, cur, n, p, blob, blob_cap, ws, ws_bytes, &P);
+  if (rc) return rc;
+  P.sms = device_sms();
+  if (P.sms <= 0) return NUMARCK_ERR_CUDA;
+  return launch_compress(P, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int numarck_read_header(const void* header_host, numarck_header* out) {

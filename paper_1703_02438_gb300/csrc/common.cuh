@@ -43,7 +43,7 @@ struct Ctrl {
   unsigned int bmin_key;        // max over binnable points of (KEY_BIAS - bin)
   unsigned int bmax_key;        // max over binnable points of (bin + KEY_BIAS)
   unsigned long long amin_key;  // ANCHOR_MIN: max of ~orderable(ratio)
-  unsigned int ticket;          // K3 dynamic tile counter (reset by K1)
+  unsigned int ticket;          // order of the offset-scan CTAs (reset by K1)
   int error;                    // device-side NUMARCK_ERR_* of the current call
   // written by K2 for K3 (plain stores; no reset needed)
   int any;                      // 1 if at least one point is binnable
@@ -290,6 +290,36 @@ __device__ __forceinline__ bool ratio_estimate(unsigned ph, unsigned pl, int ep,
   return e32 < 255;
 }
 
+// Fast part of classify_f64: 1 and the bin, 0 (not binnable), or 2 when only the exact float64
+// sequence can decide (classify_exact then gives the answer). Never calls the exact sequence.
+__device__ __forceinline__ int classify_f64_fast(double p, double x, const Consts<double>& c,
+                                                 int& b) {
+  const unsigned ph = (unsigned)__double2hiint(p), pl = (unsigned)__double2loint(p);
+  const unsigned xh = (unsigned)__double2hiint(x);
+  const int ep = (int)((ph >> 20) & 0x7FFu);
+  const int ex = (int)((xh >> 20) & 0x7FFu);
+  if ((unsigned)(ep - 200) <= 1740u && ex != 0x7FF) {
+    float Df;
+    if (!ratio_estimate(ph, pl, ep, p, x, Df)) return 0;   // |d/s| >= 2^128: far beyond the cap
+    const float aD = fabsf(Df);
+    if (aD > c.cap_hi) return 0;                           // certainly |ratio| > cap
+    if (aD <= c.cap_lo) {                                  // certainly binnable
+      const float uf = __fmul_rn(__fsub_rn(Df, c.af), c.inv_wf);
+      const float eps = __fmaf_ru(0x1.8p-20f, fabsf(uf), c.K0);
+      const float lo = floorf(__fsub_rd(uf, eps));
+      const float hi = floorf(__fadd_ru(uf, eps));
+      if (lo == hi && lo < 4194304.0f) {
+        b = __float_as_int(__fadd_rn(lo, 12582912.0f)) - 0x4B400000;   // exact for |lo| < 2^22
+        return 1;
+      }
+    }
+    return 2;
+  }
+  if ((ph << 1) == 0u && pl == 0u) return 0;               // p = +-0: ratio is +-inf or NaN
+  if (ep == 0x7FF || ex == 0x7FF) return 0;                // non-finite input
+  return 2;
+}
+
 // Bin of (p, x) for float64: 1 and the bin if binnable, else 0. Equal to classify_exact<double>.
 __device__ __forceinline__ int classify_f64(double p, double x, const Consts<double>& c, int& b) {
   const unsigned ph = (unsigned)__double2hiint(p), pl = (unsigned)__double2loint(p);
@@ -331,6 +361,28 @@ __device__ __forceinline__ int classify_f64(double p, double x, const Consts<dou
 // deltaH = 2^-21 H + 2^-20 Ef |Df| + 2^-100 covers the second. If |G| + delta < H - deltaH the
 // exact check passes; if |G| - delta > H + deltaH it fails; otherwise the exact float64 check
 // decides. (All bound arithmetic rounds away from the decision.)
+// 1 = the check passes, 0 = it fails, 2 = the estimate cannot decide (then run check_exact).
+__device__ __forceinline__ int check_f64_fast(double p, double x, float cf,
+                                              const Consts<double>& c) {
+  const unsigned ph = (unsigned)__double2hiint(p), pl = (unsigned)__double2loint(p);
+  const unsigned xh = (unsigned)__double2hiint(x);
+  const int ep = (int)((ph >> 20) & 0x7FFu);
+  const int ex = (int)((xh >> 20) & 0x7FFu);
+  float Df;
+  const bool est = ratio_estimate(ph, pl, ep, p, x, Df);
+  const float aDf = fabsf(Df);
+  const float G = __fsub_rn(cf, Df);
+  const float aG = fabsf(G);
+  const float H = __fmul_rn(c.Ef, fabsf(__fadd_rn(1.0f, Df)));
+  const float delta = __fmaf_ru(0x1p-23f, __fadd_ru(fabsf(cf), aG),
+                                __fmaf_ru(0x1p-20f, aDf, __fmaf_ru(0x1p-50f, fabsf(cf), 0x1p-49f)));
+  const float dH = __fmaf_ru(0x1p-21f, H, __fmaf_ru(0x1p-20f * c.Ef, aDf, 0x1p-100f));
+  const bool in_range = (unsigned)(ep - 200) <= 1740u && (unsigned)(ex - 100) <= 1840u && est;
+  const bool yes = __fadd_ru(aG, delta) < __fsub_rd(H, dH);
+  const bool no = __fsub_rd(aG, delta) > __fadd_ru(H, dH);
+  return !in_range ? 2 : (yes ? 1 : (no ? 0 : 2));
+}
+
 __device__ __forceinline__ bool check_f64(double p, double x, double m, float cf,
                                           const Consts<double>& c) {
   const unsigned ph = (unsigned)__double2hiint(p), pl = (unsigned)__double2loint(p);

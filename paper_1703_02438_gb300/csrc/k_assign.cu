@@ -44,42 +44,63 @@ struct RankView {
 };
 
 // Index of one element from its bin code (§III.C): M unless binnable, in a selected bin, and the
-// error check passes. Codes outside the code window are classified again (rare).
+// error check passes. fast() never calls the exact float64 sequences: it returns UNDECIDED for
+// the rare points whose bin code lies outside the code window or whose check the float32
+// estimate cannot decide; exact() settles those afterwards.
+constexpr unsigned UNDECIDED = 0x10000u;   // above every index (indices are < 2^16)
+
 template <typename T>
 struct Assigner;
 
 template <>
 struct Assigner<float> {
-  __device__ __forceinline__ static unsigned run(float p, float x, unsigned code, int cbase,
-                                                 const Consts<float>& c, const RankView& rv,
-                                                 const float* s_m, const float*, const float* g_m,
-                                                 const float*, unsigned M) {
+  __device__ __forceinline__ static unsigned fast(float p, float x, unsigned code, int cbase,
+                                                  const Consts<float>& c, const RankView& rv,
+                                                  const float* s_m, const float*,
+                                                  const float* g_m, const float*, unsigned M) {
+    if (code == CODE_NONE) return M;
+    if (code == CODE_FAR) return UNDECIDED;
+    const unsigned r = rv.lookup(cbase + (int)code);
+    if (r == M) return M;
+    const float m = r < (unsigned)MT_SMEM ? s_m[r] : g_m[r];
+    return check_exact<float>(p, x, m, c.E_T) ? r : M;
+  }
+  __device__ static unsigned exact(float p, float x, unsigned code, int cbase,
+                                   const Consts<float>& c, const RankView& rv, const float* g_m,
+                                   const float*, unsigned M) {
     if (code == CODE_NONE) return M;
     int b = cbase + (int)code;
     if (code == CODE_FAR && !classify_exact<float>(p, x, c, b)) return M;
     const unsigned r = rv.lookup(b);
     if (r == M) return M;
-    const float m = r < (unsigned)MT_SMEM ? s_m[r] : g_m[r];
-    return check_exact<float>(p, x, m, c.E_T) ? r : M;
+    return check_exact<float>(p, x, g_m[r], c.E_T) ? r : M;
   }
 };
 
 template <>
 struct Assigner<double> {
-  __device__ __forceinline__ static unsigned run(double p, double x, unsigned code, int cbase,
-                                                 const Consts<double>& c, const RankView& rv,
-                                                 const double* s_m, const float* s_cf,
-                                                 const double* g_m, const float* g_cf,
-                                                 unsigned M) {
+  __device__ __forceinline__ static unsigned fast(double p, double x, unsigned code, int cbase,
+                                                  const Consts<double>& c, const RankView& rv,
+                                                  const double* s_m, const float* s_cf,
+                                                  const double* g_m, const float* g_cf,
+                                                  unsigned M) {
+    if (code == CODE_NONE) return M;
+    if (code == CODE_FAR) return UNDECIDED;
+    const unsigned r = rv.lookup(cbase + (int)code);
+    if (r == M) return M;
+    const float cf = r < (unsigned)MT_SMEM ? s_cf[r] : g_cf[r];
+    const int d = check_f64_fast(p, x, cf, c);
+    return d == 1 ? r : (d == 0 ? M : UNDECIDED);
+  }
+  __device__ static unsigned exact(double p, double x, unsigned code, int cbase,
+                                   const Consts<double>& c, const RankView& rv, const double* g_m,
+                                   const float* g_cf, unsigned M) {
     if (code == CODE_NONE) return M;
     int b = cbase + (int)code;
     if (code == CODE_FAR && !classify_f64(p, x, c, b)) return M;
     const unsigned r = rv.lookup(b);
     if (r == M) return M;
-    const bool sm = r < (unsigned)MT_SMEM;
-    const double m = sm ? s_m[r] : g_m[r];
-    const float cf = sm ? s_cf[r] : g_cf[r];
-    return check_f64(p, x, m, cf, c) ? r : M;
+    return check_f64(p, x, g_m[r], g_cf[r], c) ? r : M;
   }
 };
 
@@ -170,9 +191,10 @@ __global__ void __launch_bounds__(K3_THREADS, 2) k3_assign(AssignArgs<T> A) {
     unsigned char* tile_out = A.blob + g.off_index + q * g.block_stride + t * (long long)(SUB / 8 * B);
 
     int count = 0;
-    unsigned my_ball = 0;      // lane l keeps the ballot of step (c0/32 + l) of the chunk
     for (int c0 = 0; c0 < cnt; c0 += K3_CHUNK) {
       const int ccnt = min(K3_CHUNK, cnt - c0);
+      unsigned my_ball = 0;   // lane l: incompressible ballot of step l of the chunk
+      unsigned my_und = 0;    // lane l: undecided ballot of step l of the chunk
       for (int i0 = 0; i0 < K3_CHUNK / 32; i0 += K3_UNROLL) {
         T pv[K3_UNROLL], xv[K3_UNROLL];
         unsigned cv[K3_UNROLL];
@@ -191,16 +213,34 @@ __global__ void __launch_bounds__(K3_THREADS, 2) k3_assign(AssignArgs<T> A) {
 #pragma unroll
         for (int u = 0; u < K3_UNROLL; ++u) {
           const int e = (i0 + u) * 32 + lane;
-          unsigned idx = 0;
-          if (e < ccnt)
-            idx = any ? Assigner<T>::run(pv[u], xv[u], cv[u], cbase, c, rv, s_m, s_cf, A.mtab,
-                                         A.cftab, M)
-                      : M;
-          my_idx[e] = (unsigned short)idx;
+          unsigned idx = M;
+          if (any) idx = Assigner<T>::fast(pv[u], xv[u], cv[u], cbase, c, rv, s_m, s_cf, A.mtab,
+                                           A.cftab, M);
+          const bool und = e < ccnt && idx == UNDECIDED;
+          my_idx[e] = (unsigned short)(und ? 0u : idx);
           const unsigned ball = __ballot_sync(0xffffffffu, e < ccnt && idx == M);
-          if (lane == i0 + u) my_ball = ball;
+          const unsigned uball = __ballot_sync(0xffffffffu, und);
+          if (lane == i0 + u) { my_ball = ball; my_und = uball; }
           count += __popc(ball);
         }
+      }
+      // settle the undecided points exactly (rare): reload them, decide, patch the ballots
+      unsigned pending = __ballot_sync(0xffffffffu, my_und != 0u);
+      while (pending) {
+        const int st = __ffs(pending) - 1;
+        pending &= pending - 1;
+        const unsigned u = __shfl_sync(0xffffffffu, my_und, st);
+        bool mk = false;
+        if ((u >> lane) & 1u) {
+          const int e = st * 32 + lane;
+          const unsigned idx = Assigner<T>::exact(pt[c0 + e], xt[c0 + e], ct[c0 + e], cbase, c,
+                                                  rv, A.mtab, A.cftab, M);
+          my_idx[e] = (unsigned short)idx;
+          mk = idx == M;
+        }
+        const unsigned fix = __ballot_sync(0xffffffffu, mk);
+        if (lane == st) my_ball |= fix;
+        count += __popc(fix);
       }
       __syncwarp();
       // the chunk's ballots, as 16-bit halves over the tile's consumed codes
@@ -210,20 +250,22 @@ __global__ void __launch_bounds__(K3_THREADS, 2) k3_assign(AssignArgs<T> A) {
         if (s0 * 32 + 16 < cnt) halves[2 * s0 + 1] = (unsigned short)(my_ball >> 16);
       }
       // bit-pack the chunk: index e at bits [e*B, e*B + B) of the tile, LSB first; the image
-      // of the tile is padded with zero bytes to a multiple of 16
+      // of the tile is padded with zero bytes to a multiple of 16. floor(v / B) for v < 2^15
+      // is (v * ceil(2^20 / B)) >> 20 exactly (the error stays below 1/32 < 1 - (B-1)/B).
       const int nwords = ((((ccnt * B + 7) >> 3) + 15) >> 4) * 4;
       unsigned* out = reinterpret_cast<unsigned*>(tile_out + (long long)(c0 / 8) * B);
+      const unsigned rB = ((1u << 20) + (unsigned)B - 1u) / (unsigned)B;
       for (int w = lane; w < nwords; w += 32) {
-        const int bit0 = w * 32;
-        int e = bit0 / B;
-        const int e_end = min((bit0 + 31) / B, ccnt - 1);
-        unsigned long long acc = 0;
+        const unsigned bit0 = (unsigned)w * 32u;
+        int e = (int)(((unsigned long long)bit0 * rB) >> 20);
+        const int e_end = min((int)(((unsigned long long)(bit0 + 31u) * rB) >> 20), ccnt - 1);
+        unsigned acc = 0;
         for (; e <= e_end; ++e) {
-          const int sh = e * B - bit0;
-          const unsigned long long xx = my_idx[e];
+          const int sh = e * B - (int)bit0;
+          const unsigned xx = my_idx[e];
           acc |= sh >= 0 ? (xx << sh) : (xx >> (-sh));
         }
-        out[w] = (unsigned)acc;
+        out[w] = acc;
       }
       __syncwarp();
     }
@@ -233,51 +275,108 @@ __global__ void __launch_bounds__(K3_THREADS, 2) k3_assign(AssignArgs<T> A) {
 
 // K3b — the incompressible offsets (§IV.C): exclusive prefix of the per-tile counts gives the
 // sub-block table; its entries at block starts give the per-block table; the total is n_inc.
-// One CTA of 1024 threads; each thread scans a contiguous run of tiles.
-__global__ void __launch_bounds__(1024, 1) k3_scan(const unsigned long long* counts, Geometry g,
-                                                  unsigned char* blob, int L) {
+// Single pass: CTA k (taken in order from a ticket counter) scans 4096 counts with coalesced
+// loads, publishes its aggregate, and finds the counts before it by a decoupled look-back over
+// the aggregates of the CTAs before it (their work is tiny, so the waits are short; every wait
+// is bounded and reports NUMARCK_ERR_TIMEOUT in the blob status on expiry).
+constexpr int SC_THREADS = 1024;
+constexpr int SC_PER = 4;
+constexpr int SC_TILE = SC_THREADS * SC_PER;
+constexpr unsigned long long SC_AGG = 1ull << 62, SC_INC = 2ull << 62, SC_VAL = (1ull << 62) - 1;
+constexpr unsigned long long SC_LIMIT_NS = 2000000000ull;
+
+__global__ void __launch_bounds__(SC_THREADS, 1) k3_scan(const unsigned long long* counts,
+                                                        unsigned long long* flags, Ctrl* ctrl,
+                                                        Geometry g, unsigned char* blob, int L) {
   __shared__ long long s_w[33];
+  __shared__ long long s_P;
+  __shared__ long long s_blk;
   const int tid = (int)threadIdx.x;
-  const long long per = (g.nsub + 1023) / 1024;
-  const long long lo = min((long long)g.nsub, tid * per), hi = min((long long)g.nsub, lo + per);
+  if (tid == 0) s_blk = (long long)atomicAdd(&ctrl->ticket, 1u);
+  __syncthreads();
+  const long long blk = s_blk;
+  const long long lo = blk * SC_TILE + (long long)tid * SC_PER;
+  long long v[SC_PER];
   long long sum = 0;
-  for (long long i = lo; i < hi; ++i) sum += (long long)counts[i];
-  // block exclusive scan of the per-thread sums
+#pragma unroll
+  for (int k = 0; k < SC_PER; ++k) {
+    v[k] = (lo + k < g.nsub) ? (long long)counts[lo + k] : 0;
+    sum += v[k];
+  }
+  // block inclusive scan of the per-thread sums
   const int lane = (int)lane_id(), w = tid >> 5;
   long long inc = sum;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const long long v = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += v;
+    const long long u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
   }
   if (lane == 31) s_w[w] = inc;
   __syncthreads();
   if (w == 0) {
-    const long long v = s_w[lane];
-    long long vi = v;
+    const long long x = s_w[lane];
+    long long xi = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const long long u = __shfl_up_sync(0xffffffffu, vi, o);
-      if (lane >= o) vi += u;
+      const long long u = __shfl_up_sync(0xffffffffu, xi, o);
+      if (lane >= o) xi += u;
     }
-    s_w[lane] = vi - v;
-    if (lane == 31) s_w[32] = vi;
+    s_w[lane] = xi - x;
+    if (lane == 31) s_w[32] = xi;
   }
   __syncthreads();
-  long long run = s_w[w] + inc - sum;
+  if (tid == 0) {
+    const long long agg = s_w[32];
+    int* blob_status = reinterpret_cast<int*>(blob + offsetof(numarck_header, status));
+    long long P = 0;
+    if (blk == 0) {
+      st_relaxed_u64(&flags[0], SC_INC | (unsigned long long)agg);
+    } else {
+      st_relaxed_u64(&flags[blk], SC_AGG | (unsigned long long)agg);
+      long long j = blk - 1;
+      unsigned spins = 0;
+      unsigned long long t0 = 0;
+      while (j >= 0) {
+        const unsigned long long sv = ld_relaxed_u64(&flags[j]);
+        const unsigned long long f = sv >> 62;
+        if (f == 0) {
+          if (++spins == 64) t0 = global_timer_ns();
+          if (spins > 64) {
+            __nanosleep(100);
+            if ((spins & 63u) == 0 && global_timer_ns() - t0 > SC_LIMIT_NS) {
+              atomicExch(blob_status, NUMARCK_ERR_TIMEOUT);
+              break;
+            }
+          }
+          continue;
+        }
+        P += (long long)(sv & SC_VAL);
+        if (f == 2) break;
+        --j;
+      }
+      st_relaxed_u64(&flags[blk], SC_INC | (unsigned long long)(P + agg));
+    }
+    s_P = P;
+  }
+  __syncthreads();
+  long long run = s_P + s_w[w] + inc - sum;
   int64_t* sub_off = reinterpret_cast<int64_t*>(blob + g.off_sub_off);
   int64_t* inc_off = reinterpret_cast<int64_t*>(blob + g.off_inc_off);
-  for (long long i = lo; i < hi; ++i) {
-    sub_off[i] = run;
-    if (i % g.spb == 0) inc_off[i / g.spb] = run;
-    run += (long long)counts[i];
-  }
-  if (tid == 0) {
-    const long long n_inc = s_w[32];
-    inc_off[g.nblocks] = n_inc;
-    numarck_header* h = reinterpret_cast<numarck_header*>(blob);
-    h->n_inc = n_inc;
-    h->total_bytes = g.off_exact + n_inc * (long long)L;
+#pragma unroll
+  for (int k = 0; k < SC_PER; ++k) {
+    const long long i = lo + k;
+    if (i < g.nsub) {
+      sub_off[i] = run;
+      if (i % g.spb == 0) inc_off[i / g.spb] = run;
+      if (i == g.nsub - 1) {
+        const long long n_inc = run + v[k];
+        inc_off[g.nblocks] = n_inc;
+        numarck_header* h = reinterpret_cast<numarck_header*>(blob);
+        h->n_inc = n_inc;
+        h->total_bytes = g.off_exact + n_inc * (long long)L;
+      }
+      run += v[k];
+    }
   }
 }
 
@@ -313,16 +412,24 @@ __global__ void __launch_bounds__(512) k3_exact(const T* __restrict__ cur,
     }
     __syncwarp();
     long long run = sub_off[gt];
+    // steps in groups of 8: the gathers of a group are in flight together before its stores
 #pragma unroll
     for (int k = 0; k < STEPS / 32; ++k) {
-      unsigned any = __ballot_sync(0xffffffffu, mine[k] != 0u);
-      while (any) {
-        const int s = __ffs(any) - 1;
-        any &= any - 1;
-        const unsigned ball = __shfl_sync(0xffffffffu, mine[k], s);
-        if ((ball >> lane) & 1u)
-          exact_u[run + __popc(ball & lanemask_lt())] = xu[j0 + (long long)(k * 32 + s) * 32 + lane];
-        run += __popc(ball);
+#pragma unroll
+      for (int s0 = 0; s0 < 32; s0 += 8) {
+        unsigned ball[8];
+        U val[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          ball[u] = __shfl_sync(0xffffffffu, mine[k], s0 + u);
+          val[u] = 0;
+          if ((ball[u] >> lane) & 1u) val[u] = xu[j0 + (long long)(k * 32 + s0 + u) * 32 + lane];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if ((ball[u] >> lane) & 1u) exact_u[run + __popc(ball[u] & lanemask_lt())] = val[u];
+          run += __popc(ball[u]);
+        }
       }
     }
   }
@@ -368,8 +475,11 @@ static cudaError_t launch_assign_t(const CompressPlan& P, cudaStream_t s, const 
 
 cudaError_t launch_offsets(const CompressPlan& P, cudaStream_t s) {
   if (P.g.nsub == 0) return cudaSuccess;
-  k3_scan<<<1, 1024, 0, s>>>(reinterpret_cast<const unsigned long long*>(P.ws + P.wl.status), P.g,
-                             P.blob, P.g.dtype == NUMARCK_F64 ? 8 : 4);
+  const long long nblk = (P.g.nsub + SC_TILE - 1) / SC_TILE;
+  auto* counts = reinterpret_cast<const unsigned long long*>(P.ws + P.wl.status);
+  auto* flags = reinterpret_cast<unsigned long long*>(P.ws + P.wl.status) + P.g.nsub;
+  k3_scan<<<(unsigned)nblk, SC_THREADS, 0, s>>>(counts, flags, reinterpret_cast<Ctrl*>(P.ws + P.wl.ctrl),
+                                                P.g, P.blob, P.g.dtype == NUMARCK_F64 ? 8 : 4);
   return cudaGetLastError();
 }
 

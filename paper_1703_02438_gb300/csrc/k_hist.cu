@@ -90,16 +90,23 @@ __device__ __forceinline__ void hist_add(const HistCtx& h, bool valid, int b) {
 template <typename T>
 struct Classifier;
 
+// fast(): 1 (binnable, bin in b), 0 (not binnable) or 2 (undecided: call exact()).
 template <>
 struct Classifier<float> {
-  __device__ __forceinline__ static int run(float p, float x, const Consts<float>& c, int& b) {
+  __device__ __forceinline__ static int fast(float p, float x, const Consts<float>& c, int& b) {
+    return classify_exact<float>(p, x, c, b);
+  }
+  __device__ static int exact(float p, float x, const Consts<float>& c, int& b) {
     return classify_exact<float>(p, x, c, b);
   }
 };
 template <>
 struct Classifier<double> {
-  __device__ __forceinline__ static int run(double p, double x, const Consts<double>& c, int& b) {
-    return classify_f64(p, x, c, b);
+  __device__ __forceinline__ static int fast(double p, double x, const Consts<double>& c, int& b) {
+    return classify_f64_fast(p, x, c, b);
+  }
+  __device__ static int exact(double p, double x, const Consts<double>& c, int& b) {
+    return classify_exact_f64_slow(p, x, c, &b);
   }
 };
 
@@ -126,7 +133,7 @@ constexpr int K1_THREADS = 512;
 constexpr int K1_UNROLL = 4;
 
 template <typename T, bool VEC>
-__global__ void __launch_bounds__(K1_THREADS) k1_hist(const T* __restrict__ prev,
+__global__ void __launch_bounds__(K1_THREADS, 2) k1_hist(const T* __restrict__ prev,
                                                       const T* __restrict__ cur, int64_t n,
                                                       Consts<T> c, int anchor_min, Ctrl* ctrl,
                                                       unsigned long long* hist,
@@ -143,9 +150,10 @@ __global__ void __launch_bounds__(K1_THREADS) k1_hist(const T* __restrict__ prev
   if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->code_base = h.cbase;
 
   for (int i = threadIdx.x; i < SH_BINS; i += blockDim.x) sh[i] = 0u;
-  // K3's scan state and tile counter for this call
+  // this call's per-tile counts, offset-scan flags and scan ticket start at zero
   if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->ticket = 0u;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nsub;
+  const int64_t nstat = nsub > 0 ? nsub + nsub / 4096 + 2 : 0;   // counts + scan flags
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nstat;
        i += (int64_t)gridDim.x * blockDim.x)
     tstatus[i] = 0ull;
   __syncthreads();
@@ -173,17 +181,40 @@ __global__ void __launch_bounds__(K1_THREADS) k1_hist(const T* __restrict__ prev
         V::get(a, pe[u]);
         V::get(b, xe[u]);
       }
+      unsigned pend = 0;   // bit u * V::N + v: element needs the exact sequence
 #pragma unroll
       for (int u = 0; u < K1_UNROLL; ++u) {
         const int64_t vi = base + u * 32 + lane;
 #pragma unroll
         for (int v = 0; v < V::N; ++v) {
           int b = 0;
-          const bool binned = ok[u] && Classifier<T>::run(pe[u][v], xe[u][v], c, b);
+          const int kind = ok[u] ? Classifier<T>::fast(pe[u][v], xe[u][v], c, b) : 0;
+          const bool binned = kind == 1;
           if (binned) { lmin = min(lmin, b); lmax = max(lmax, b); }
-          if (ok[u]) codes[vi * V::N + v] = bin_code(h, binned, b);
+          if (kind == 2) pend |= 1u << (u * V::N + v);
+          else if (ok[u]) codes[vi * V::N + v] = bin_code(h, binned, b);
           hist_add(h, binned, b);
         }
+      }
+      // settle undecided elements (rare) with the exact sequence, one per lane per round
+      while (__any_sync(0xffffffffu, pend != 0u)) {
+        int b = 0;
+        bool binned = false;
+        if (pend) {
+          const int k = __ffs(pend) - 1;
+          pend &= pend - 1;
+          const int u = k / V::N, v = k % V::N;
+          T pk = pe[0][0], xk = xe[0][0];
+#pragma unroll
+          for (int uu = 0; uu < K1_UNROLL; ++uu)
+#pragma unroll
+            for (int vv = 0; vv < V::N; ++vv)
+              if (uu == u && vv == v) { pk = pe[uu][vv]; xk = xe[uu][vv]; }
+          binned = Classifier<T>::exact(pk, xk, c, b) == 1;
+          codes[(base + u * 32 + lane) * V::N + v] = bin_code(h, binned, b);
+          if (binned) { lmin = min(lmin, b); lmax = max(lmax, b); }
+        }
+        hist_add(h, binned, b);
       }
     }
     // scalar tail (< V elements), one warp
@@ -192,7 +223,7 @@ __global__ void __launch_bounds__(K1_THREADS) k1_hist(const T* __restrict__ prev
       const int64_t j = t0 + lane;
       int b = 0;
       bool binned = false;
-      if (j < n) binned = Classifier<T>::run(ld_stream(prev + j), ld_stream(cur + j), c, b);
+      if (j < n) binned = Classifier<T>::exact(ld_stream(prev + j), ld_stream(cur + j), c, b) == 1;
       if (binned) { lmin = min(lmin, b); lmax = max(lmax, b); }
       if (j < n) codes[j] = bin_code(h, binned, b);
       hist_add(h, binned, b);
@@ -212,7 +243,7 @@ __global__ void __launch_bounds__(K1_THREADS) k1_hist(const T* __restrict__ prev
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         int b = 0;
-        const bool binned = ok[u] && Classifier<T>::run(pe[u], xe[u], c, b);
+        const bool binned = ok[u] && Classifier<T>::exact(pe[u], xe[u], c, b) == 1;
         if (binned) { lmin = min(lmin, b); lmax = max(lmax, b); }
         if (ok[u]) codes[base + u * 32 + lane] = bin_code(h, binned, b);
         hist_add(h, binned, b);

@@ -41,4 +41,13 @@ cudaError_t launch_offsets(const CompressPlan& P, cudaStream_t s);     // K3b: o
 cudaError_t launch_exact(const CompressPlan& P, cudaStream_t s);       // K3c: incompressible values
 cudaError_t launch_decode(const DecodePlan& P, cudaStream_t s);        // K4 / K5
 
+// Host-side planning shared by the single-variable and batched entry points (capi.cu).
+int plan_compress(const void* prev, const void* cur, int64_t n, const numarck_params* p,
+                  void* blob, size_t blob_cap, void* ws, size_t ws_bytes, CompressPlan* out);
+int launch_compress(const CompressPlan& P, cudaStream_t s);
+int plan_decompress_check(const void* blob, const void* prev, void* out, int64_t n);
+int launch_decompress(const void* blob, const void* prev, void* out, int64_t n, int32_t* status,
+                      int sms, cudaStream_t s);
+int current_device_sms();
+
 }  // namespace nmk

@@ -48,6 +48,16 @@ class Params(ctypes.Structure):
                 ("block_bytes", ctypes.c_int64)]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("prev", ctypes.c_void_p), ("cur", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("params", Params), ("blob", ctypes.c_void_p), ("blob_cap", ctypes.c_size_t)]
+
+
+class BatchDecodeItem(ctypes.Structure):
+    _fields_ = [("blob", ctypes.c_void_p), ("prev", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("n", ctypes.c_int64)]
+
+
 _lib = None
 
 
@@ -81,6 +91,15 @@ def lib() -> ctypes.CDLL:
         L.numarck_status_string.restype = ctypes.c_char_p
         L.numarck_trace_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), i32]
         L.numarck_trace_events.restype = i32
+        L.numarck_batch_workspace_bytes.argtypes = [ctypes.POINTER(BatchItem), i32, i32]
+        L.numarck_batch_workspace_bytes.restype = sz
+        L.numarck_compress_batch.argtypes = [ctypes.POINTER(BatchItem), i32, i32, i32, vp, sz, vp]
+        L.numarck_compress_batch.restype = i32
+        L.numarck_decompress_batch.argtypes = [ctypes.POINTER(BatchDecodeItem), i32, i32, i32, vp,
+                                               vp]
+        L.numarck_decompress_batch.restype = i32
+        L.numarck_compress_noalloc.argtypes = [vp, vp, i64, pp, vp, sz, vp]
+        L.numarck_compress_noalloc.restype = i32
         L.numarck_version.argtypes = []
         L.numarck_version.restype = ctypes.c_char_p
         _lib = L
@@ -213,6 +232,76 @@ def decompress_range(blob: torch.Tensor, prev_seg: torch.Tensor, start: int, cou
                                           ctypes.c_void_p(_stream_ptr(stream))),
            "numarck_decompress_range")
     return out
+
+
+class Batch:
+    """A fixed list of variables to compress together (see numarck_compress_batch).
+
+    pairs: list of (prev, cur) 1-D CUDA tensors; specs: list of (E, B) or (E, B, anchor,
+    block_bytes) per variable. Blob buffers are allocated once (compress_bound bytes each) and
+    reused by every run, so a run can be captured into a CUDA graph."""
+
+    def __init__(self, pairs, specs, lanes=8, grid_share=4, workspace=None):
+        self.pairs = [(p.contiguous(), x.contiguous()) for p, x in pairs]
+        self.lanes, self.grid_share = int(lanes), int(grid_share)
+        arr = (BatchItem * len(pairs))()
+        self.blobs = []
+        for i, ((p, x), spec) in enumerate(zip(self.pairs, specs)):
+            E, B = spec[0], spec[1]
+            anchor = spec[2] if len(spec) > 2 else ANCHOR_ZERO
+            bb = spec[3] if len(spec) > 3 else 0
+            prm = make_params(p.dtype, B, E, anchor, bb)
+            bound = compress_bound(p.numel(), prm)
+            if bound == 0:
+                raise NumarckError(ERR_INVALID_ARG, f"batch item {i}")
+            blob = torch.empty(bound, dtype=torch.uint8, device=p.device)
+            self.blobs.append(blob)
+            arr[i] = BatchItem(p.data_ptr(), x.data_ptr(), p.numel(), prm, blob.data_ptr(), bound)
+        self.items = arr
+        self.count = len(pairs)
+        self.ws = workspace or Workspace(self.pairs[0][0].device if self.pairs else "cuda")
+
+    def set_lanes(self, lanes, grid_share):
+        self.lanes, self.grid_share = int(lanes), int(grid_share)
+
+    def run(self, stream=None):
+        """Queues the compression of every variable; returns the list of blob buffers."""
+        need = int(lib().numarck_batch_workspace_bytes(self.items, self.count, self.lanes))
+        if need == 0 and self.count:
+            raise NumarckError(ERR_INVALID_ARG, "numarck_batch_workspace_bytes")
+        ws = self.ws.get(need, stream)
+        _check(lib().numarck_compress_batch(self.items, self.count, self.lanes, self.grid_share,
+                                            ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                            ctypes.c_void_p(_stream_ptr(stream))),
+               "numarck_compress_batch")
+        return self.blobs
+
+
+def decompress_batch(blobs, prevs, outs=None, lanes=8, grid_share=4, status=None, stream=None):
+    """Reconstructs every variable of a batch (one blob and one prev per variable)."""
+    outs = outs or [torch.empty_like(p) for p in prevs]
+    arr = (BatchDecodeItem * len(blobs))()
+    for i, (b, p, o) in enumerate(zip(blobs, prevs, outs)):
+        arr[i] = BatchDecodeItem(b.data_ptr(), p.data_ptr(), o.data_ptr(), p.numel())
+    sp = ctypes.c_void_p(status.data_ptr()) if status is not None else None
+    _check(lib().numarck_decompress_batch(arr, len(blobs), int(lanes), int(grid_share), sp,
+                                          ctypes.c_void_p(_stream_ptr(stream))),
+           "numarck_decompress_batch")
+    return outs
+
+
+def compress_noalloc(prev, cur, E, B, anchor=ANCHOR_ZERO, block_bytes=0, blob=None, stream=None):
+    """numarck_compress_noalloc: compression without a caller workspace (static scratch)."""
+    params = make_params(prev.dtype, B, E, anchor, block_bytes)
+    if blob is None:
+        blob = torch.empty(compress_bound(prev.numel(), params), dtype=torch.uint8,
+                           device=prev.device)
+    _check(lib().numarck_compress_noalloc(ctypes.c_void_p(prev.data_ptr()),
+                                          ctypes.c_void_p(cur.data_ptr()), prev.numel(),
+                                          ctypes.byref(params), ctypes.c_void_p(blob.data_ptr()),
+                                          blob.numel(), ctypes.c_void_p(_stream_ptr(stream))),
+           "numarck_compress_noalloc")
+    return blob
 
 
 _trace_keep = None

@@ -48,20 +48,37 @@ def _gen(device, seed: int) -> torch.Generator:
 # Plain 1-D pair
 # ----------------------------------------------------------------------------------------
 def plain_pair(n: int = 1 << 20, seed: int = seed_for(0), dtype=torch.float64,
-               zero_frac: float = 0.01, scale: float = 1.0):
-    """(prev, cur) as CPU tensors of `dtype`. Generated in float64 on the host, then cast."""
-    g = _gen("cpu", seed)
-    prev = torch.empty(n, dtype=torch.float64).log_normal_(0.0, 1.0, generator=g)
+               zero_frac: float = 0.01, scale: float = 1.0, device="cpu"):
+    """(prev, cur) as tensors of `dtype` on `device` (generated in float64, then cast)."""
+    g = _gen(device, seed)
+    kw = dict(generator=g, dtype=torch.float64, device=device)
+    prev = torch.empty(n, dtype=torch.float64, device=device).log_normal_(0.0, 1.0, generator=g)
     nz = int(round(zero_frac * n))
     if nz:
-        prev[torch.randperm(n, generator=g)[:nz]] = 0.0
-    pick = torch.rand(n, generator=g, dtype=torch.float64)
-    r1 = torch.randn(n, generator=g, dtype=torch.float64) * 1e-3
-    r2 = 8e-3 + torch.randn(n, generator=g, dtype=torch.float64) * 2e-3
-    r3 = torch.rand(n, generator=g, dtype=torch.float64) - 0.5
+        prev[torch.randperm(n, generator=g, device=device)[:nz]] = 0.0
+    pick = torch.rand(n, **kw)
+    r1 = torch.randn(n, **kw) * 1e-3
+    r2 = 8e-3 + torch.randn(n, **kw) * 2e-3
+    r3 = torch.rand(n, **kw) - 0.5
     r = torch.where(pick < 0.6, r1, torch.where(pick < 0.9, r2, r3)) * scale
     cur = prev * (1.0 + r)
     return prev.to(dtype), cur.to(dtype)
+
+
+def batch_specs(count: int = 256, seed: int = seed_for(3), n_lo: float = 1e4, n_hi: float = 2e8):
+    """Per-variable recipe of a batch: (n, dtype, E, B, scale) with n log-uniform in
+    [n_lo, n_hi], dtype float32/float64 with equal odds, E in {1e-2, 1e-3, 1e-4}, B in
+    {6, 8, 10}, and the ratio mixture of plain_pair scaled by U(0.5, 4)."""
+    g = _gen("cpu", seed)
+    out = []
+    for _ in range(count):
+        u = torch.rand(5, generator=g, dtype=torch.float64).tolist()
+        n = int(round(math.exp(math.log(n_lo) + u[0] * (math.log(n_hi) - math.log(n_lo)))))
+        dtype = torch.float64 if u[1] < 0.5 else torch.float32
+        E = (1e-2, 1e-3, 1e-4)[min(2, int(u[2] * 3))]
+        B = (6, 8, 10)[min(2, int(u[3] * 3))]
+        out.append((n, dtype, E, B, 0.5 + 3.5 * u[4]))
+    return out
 
 
 # ----------------------------------------------------------------------------------------

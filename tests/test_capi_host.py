@@ -131,3 +131,30 @@ def test_decompress_argument_errors_before_device(lib):
     assert full(4999) == N.ERR_INVALID_ARG    # n must match the header
     assert lib.numarck_decompress(ctypes.c_void_p(A + 8), hb, ctypes.c_void_p(A),
                                   ctypes.c_void_p(A), 5000, None, None) == N.ERR_INVALID_ARG
+
+
+def test_batch_validation_before_device(lib):
+    """Batch calls validate every item on the host before queueing anything."""
+    A = 1 << 20
+    good = N.Params(N.F64, 8, 1e-3, 0, 0, 0)
+    bad = N.Params(N.F64, 0, 1e-3, 0, 0, 0)
+    n = 5000
+    bound = N.compress_bound(n, good)
+    items = (N.BatchItem * 3)(N.BatchItem(A, A, n, good, A, bound),
+                              N.BatchItem(A, A, 2 * n, good, A, N.compress_bound(2 * n, good)),
+                              N.BatchItem(A, A, n, bad, A, bound))
+    assert lib.numarck_batch_workspace_bytes(items, 3, 2) == 0          # invalid item 2
+    assert lib.numarck_batch_workspace_bytes(items, 2, 2) >= 2 * N.workspace_bytes(n, good)
+    assert lib.numarck_batch_workspace_bytes(items, 2, 1) == N.workspace_bytes(2 * n, good)
+    assert lib.numarck_batch_workspace_bytes(items, 2, 0) == 0
+    assert lib.numarck_compress_batch(items, 3, 2, 1, ctypes.c_void_p(A), 1 << 40, None) \
+        == N.ERR_INVALID_ARG
+    assert lib.numarck_compress_batch(items, 2, 2, 0, ctypes.c_void_p(A), 1 << 40, None) \
+        == N.ERR_INVALID_ARG                                              # grid_share < 1
+    need = lib.numarck_batch_workspace_bytes(items, 2, 2)
+    assert lib.numarck_compress_batch(items, 2, 2, 1, ctypes.c_void_p(A), need - 1, None) \
+        == N.ERR_CAPACITY
+    short = (N.BatchItem * 1)(N.BatchItem(A, A, n, good, A, bound - 1))
+    assert lib.numarck_compress_batch(short, 1, 1, 1, ctypes.c_void_p(A), 1 << 40, None) \
+        == N.ERR_CAPACITY
+    assert lib.numarck_compress_batch(items, 0, 1, 1, None, 0, None) == N.OK
