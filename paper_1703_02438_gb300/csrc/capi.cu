@@ -77,9 +77,13 @@ Consts<T> make_consts(double E, int anchor) {
   c.af = (float)c.a;
   c.inv_wf = (float)c.inv_w;
   c.Ef = (float)c.E_T;
+  c.wf = (float)c.w;
   c.cap_lo = f_down((double)c.cap * (1.0 - 0x1p-19));
   c.cap_hi = f_up((double)c.cap * (1.0 + 0x1p-19));
   c.K0 = f_up(0x1p-19 * (double)c.inv_w * std::fabs((double)c.a) + 0x1p-60);
+  c.kA = f_up((0x1p-22 + 0x1p-23 + 0x1p-50) * (1.0 + 0x1p-40));
+  c.k1 = f_up(0x1p-20 * (1.0 + (double)c.Ef) * (1.0 + 0x1p-40));
+  c.C0 = f_up((0x1p-22 * std::fabs((double)c.af) + 0x1p-49 + 0x1p-50 + 0x1p-100) * (1.0 + 0x1p-40));
   return c;
 }
 

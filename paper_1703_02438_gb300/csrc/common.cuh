@@ -30,12 +30,17 @@ constexpr int TILE_THREADS = 512;               // K3/K4 block size
 constexpr int EPT = SUB / TILE_THREADS;         // elements per thread per tile (8)
 constexpr int NCHUNK = EPT * (TILE_THREADS / 32); // 32-element chunks per tile (128)
 constexpr unsigned KEY_BIAS = 0x40000000u;      // bin-range keys: 0 means "no value"
-// Per-element bin codes written by K1 and read by K3: code = bin - code_base for bins within
-// 65534 of code_base (code_base = zero-change bin - 32767); CODE_FAR for binnable points outside
-// that window (K3 classifies them again), CODE_NONE for points that are not binnable.
-constexpr unsigned CODE_FAR = 0xFFFEu;
-constexpr unsigned CODE_NONE = 0xFFFFu;
-constexpr int CODE_HALF = 32767;
+// Per-element codes written by K1 and read by K3. For a binnable point whose bin b lies in the
+// code window [code_base, code_base + CODE_BINS) (code_base = zero-change bin - 16383):
+// code = (b - code_base) << 1 | pass, where pass is the error-bound check of §III.C against the
+// centre of b itself (the only centre a point can be indexed to). CODE_FAR marks binnable points
+// outside the window (K3 classifies and checks them again from prev and cur), CODE_NONE points
+// that are not binnable. CODE_NONE is even (pass bit clear) and CODE_FAR odd, and both have
+// code >> 1 = CODE_BINS, one past the last bin of the window.
+constexpr unsigned CODE_NONE = 0xFFFEu;
+constexpr unsigned CODE_FAR = 0xFFFFu;
+constexpr int CODE_BINS = 32767;
+constexpr int CODE_HALF = 16383;
 
 // Workspace control block (first 256 bytes of the workspace). Zero at entry of every
 // compression; the kernels restore the zero state of every field they accumulate into.
@@ -52,8 +57,9 @@ struct Ctrl {
   int pad0;
   double a;                     // grid anchor (the T value, widened)
   unsigned int win_err;         // a bin fell outside the histogram window (never expected)
-  int code_base;                // bin of code 0 in K1's per-element bin codes (written by K1)
-  unsigned int pad1[48];
+  int code_base;                // bin of code 0 in K1's per-point codes (written by K1)
+  int sel_lo, sel_hi;           // bin range of the selected bins (sel_lo > sel_hi: none)
+  unsigned int pad1[46];
 };
 static_assert(sizeof(Ctrl) == 256, "Ctrl must be 256 bytes");
 
@@ -109,12 +115,12 @@ __host__ __device__ inline Geometry make_geometry(int64_t n, int dtype, int B, i
 
 constexpr int64_t MAX_N = (int64_t)1 << 40;
 
-// Byte offset of K1's per-element bin codes inside the blob buffer: the tail of the
-// incompressible-value capacity (element j at + 2j). Incompressible values written for the
-// elements before any index j_e take at most j_e * L bytes, and j_e * (L - 2) <= n * (L - 2), so
-// they never reach the code of an element at or after j_e.
+// Byte offset of K1's per-element codes inside the blob buffer: the tail of the
+// incompressible-value capacity, rounded down to 16 bytes (element j at + 2j). K3a consumes a
+// tile's codes before anything is written over them (its own marker ballots); K3c reads those
+// ballots only while the incompressible table ends at or below this offset.
 __host__ __device__ __forceinline__ int64_t code_offset(const Geometry& g) {
-  return g.off_exact + g.n * ((g.dtype == NUMARCK_F64 ? 8 : 4) - 2);
+  return (g.off_exact + g.n * ((g.dtype == NUMARCK_F64 ? 8 : 4) - 2)) & ~(int64_t)15;
 }
 
 // Checks a header against the geometry its own fields imply. Returns 0 or NUMARCK_ERR_CORRUPT
@@ -146,10 +152,12 @@ template <typename T>
 struct Consts {
   T E_T, w, inv_w, cap, a;
   int hbase;      // histogram window index = bin - hbase
-  // float64 estimate: af = fl32(a), inv_wf = fl32(inv_w), Ef = fl32(E_T),
+  // float64 estimate: af = fl32(a), inv_wf = fl32(inv_w), Ef = fl32(E_T), wf = fl32(w),
   // cap_lo <= cap (1 - 2^-19), cap_hi >= cap (1 + 2^-19),
-  // K0 >= 2^-19 inv_w |a| + 2^-60 (all rounded away from the decision)
-  float af, inv_wf, Ef, cap_lo, cap_hi, K0;
+  // K0 >= 2^-19 inv_w |a| + 2^-60, and for K1's own-bin check kA >= 2^-22 + 2^-23 + 2^-50,
+  // k1 >= 2^-20 (1 + Ef), C0 >= 2^-22 |af| + 2^-49 + 2^-50 + 2^-100 (all rounded away from
+  // the decision)
+  float af, inv_wf, Ef, cap_lo, cap_hi, K0, wf, kA, k1, C0;
 };
 
 // ------------------------------------------------------------------------------------------
@@ -236,6 +244,16 @@ __device__ __forceinline__ bool check_exact(T p, T x, T m, T E_T) {
   T e = t_sub(R, x);
   T tol = t_mul(E_T, t_abs(x));
   return t_abs(e) <= tol;
+}
+
+// Centre of bin b, a + (b + 1/2) w (§III.B), and the multiplier m = 1 + centre (Eq. 4), in T.
+template <typename T>
+__device__ __forceinline__ T bin_centre(int b, T a, T w) {
+  return t_add(a, t_mul(t_add((T)b, (T)0.5), w));
+}
+template <typename T>
+__device__ __forceinline__ T bin_multiplier(int b, T a, T w) {
+  return t_add((T)1, bin_centre<T>(b, a, w));
 }
 
 static __device__ __noinline__ int classify_exact_f64_slow(double p, double x, const Consts<double>& c,
@@ -381,6 +399,61 @@ __device__ __forceinline__ int check_f64_fast(double p, double x, float cf,
   const bool yes = __fadd_ru(aG, delta) < __fsub_rd(H, dH);
   const bool no = __fsub_rd(aG, delta) > __fadd_ru(H, dH);
   return !in_range ? 2 : (yes ? 1 : (no ? 0 : 2));
+}
+
+// K1's fused float64 step: the bin of (p, x) as classify_f64_fast decides it and, for a bin in
+// the code window, the check of §III.C against that bin's own centre, decided from the same
+// ratio estimate Df. The multiplier is estimated in float32 from the bin id:
+//   v = b + 1/2 (exact), Q = fl32(v * wf), cfe = fl32(af + Q),
+// while the exact sequence uses c' = m - 1, m = fl64(1 + fl64(a + fl64(v * w))). Then
+//   |c' - (a + v w)|  <= 2^-51 (1 + |a| + 2 |v w|)                       (three roundings),
+//   |cfe - (a + v w)| <= 1.07 * 2^-24 |cfe| + 2^-24 |a| + 2.0001 * 2^-24 |v w|,
+// and as |a| <= |af| (1 + 2^-23), |v w| <= |Q| (1 + 2^-22):
+//   |cfe - c'| <= Kc = 2^-22 (|cfe| + |af| + 2 |Q|) + 2^-50               (rounded upward),
+// which takes the place of the rounding of cf in check_f64_fast's bound: the same decision rule
+// with G = fl(cfe - Df) and delta + Kc is exact. The terms of delta + Kc and dH are regrouped
+// below into one per-bin term and one term in |Df| (each rounded upward, so every comparison
+// implies the one it replaces).
+// Returns 0 (not binnable), 1 (bin, and pass when the bin is in the window, decided),
+// 2 (the bin needs the exact sequence), 3 (the bin is decided, the check needs the exact one).
+__device__ __forceinline__ int classify_check_f64_fast(double p, double x, const Consts<double>& c,
+                                                       int cbase, int& b, bool& pass) {
+  // computed without branches: every quantity below is harmless for any input bits, and the
+  // outcome is selected at the end
+  const unsigned ph = (unsigned)__double2hiint(p), pl = (unsigned)__double2loint(p);
+  const unsigned xh = (unsigned)__double2hiint(x);
+  const int ep = (int)((ph >> 20) & 0x7FFu);
+  const int ex = (int)((xh >> 20) & 0x7FFu);
+  float Df;
+  const bool est = ratio_estimate(ph, pl, ep, p, x, Df);   // false: |d/s| >= 2^128
+  const float aD = fabsf(Df);
+  const float uf = __fmul_rn(__fsub_rn(Df, c.af), c.inv_wf);
+  const float eps = __fmaf_ru(0x1.8p-20f, fabsf(uf), c.K0);
+  const float lo = floorf(__fsub_rd(uf, eps));
+  const float hi = floorf(__fadd_ru(uf, eps));
+  b = __float_as_int(__fadd_rn(lo, 12582912.0f)) - 0x4B400000;     // exact for |lo| < 2^22
+  const float Q = __fmul_rn(__fadd_rn(lo, 0.5f), c.wf);             // lo + 1/2 exact
+  const float cfe = __fadd_rn(c.af, Q);
+  // Pb >= 2^-23 |cfe| + 2^-50 |cfe| + 2^-49 + Kc + 2^-100: the parts of delta and dH that depend
+  // on the bin alone; T1 adds the parts proportional to |Df| (2^-20 (1 + Ef) |Df|)
+  const float Pb = __fmaf_ru(fabsf(cfe), c.kA, __fmaf_ru(fabsf(Q), 0x1p-21f, c.C0));
+  const float T1 = __fmaf_ru(aD, c.k1, Pb);
+  const float aG = fabsf(__fsub_rn(cfe, Df));
+  const float H = __fmul_rn(c.Ef, fabsf(__fadd_rn(1.0f, Df)));
+  // |G| + delta < H - dH, i.e. |G| (1 + 2^-23) + T1 < H (1 - 2^-21): the check passes;
+  // |G| - delta > H + dH, i.e. |G| (1 - 2^-23) > H (1 + 2^-21) + T1: it fails
+  const bool yes = __fmaf_ru(aG, 0x1.000002p+0f, T1) < __fmul_rd(H, 0x1.fffffp-1f);
+  const bool no = __fmul_rd(aG, 0x1.fffffcp-1f) > __fmaf_ru(H, 0x1.000008p+0f, T1);
+  pass = yes;
+  const bool in_range = (unsigned)(ep - 200) <= 1740u && ex != 0x7FF;   // estimate valid
+  const bool beyond = !est || aD > c.cap_hi;                             // |ratio| > cap surely
+  const bool sure = aD <= c.cap_lo && lo == hi && lo < 4194304.0f;       // bin decided
+  const bool outside = (unsigned)(b - cbase) >= (unsigned)CODE_BINS;     // no check needed
+  const bool decided = (unsigned)(ex - 100) <= 1840u && (yes || no);     // check decided
+  // p = +-0 (ratio +-inf or NaN) or a non-finite input: not binnable
+  const bool never = ((ph << 1) == 0u && pl == 0u) || ep == 0x7FF || ex == 0x7FF;
+  return in_range ? (beyond ? 0 : (!sure ? 2 : ((outside || decided) ? 1 : 3)))
+                  : (never ? 0 : 2);
 }
 
 __device__ __forceinline__ bool check_f64(double p, double x, double m, float cf,

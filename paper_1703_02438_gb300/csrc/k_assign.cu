@@ -1,14 +1,17 @@
-// k_assign.cu — K3: indexing (§III.C) fused with bit packing of the index table (§IV.C) and the
-// order-preserving compaction of incompressible values into the incompressible table, plus the
-// per-block (§IV.C) and per-sub-block offset tables.
+// k_assign.cu — K3: indexing (§III.C) and bit packing of the index table (§IV.C) from K1's
+// per-point codes (K3a), the per-block and per-sub-block offset tables of the incompressible
+// values (K3b), and the order-preserving copy of those values into the incompressible table (K3c).
 //
 // The paper assigns integer indices per rank, aligns block boundaries across ranks with MPI_Scan
 // and neighbour MPI_Send/Recv, and then bit-writes each block (§IV.C). Here a tile is one
 // 4096-element sub-block of an index block, so no tile straddles a block and no exchange is
-// needed; the only cross-tile dependency, the number of incompressible points before a tile,
-// comes from a single-pass decoupled look-back over tiles taken in order from a ticket counter
-// (every wait is bounded and reports NUMARCK_ERR_TIMEOUT in the blob status on expiry).
+// needed. The only cross-tile dependency, the number of incompressible points before a tile, is
+// a prefix sum of per-tile counts (K3b: a single-pass decoupled look-back; every wait is bounded
+// and reports NUMARCK_ERR_TIMEOUT in the blob status on expiry).
+#include <array>
 #include <cstddef>
+#include <type_traits>
+#include <utility>
 
 #include "launch.h"
 
@@ -28,49 +31,35 @@ struct AssignArgs {
   const float* cftab;
   unsigned long long* tstatus;
   unsigned char* blob;
-  const unsigned short* codes;   // K1's per-element bin codes
+  const unsigned short* codes;   // K1's per-point codes
 };
 
+// Rank of a bin from the global rank table (M if not selected; bins outside the selected range
+// are M without a lookup). Used for the points outside K1's code window.
 struct RankView {
-  const unsigned short* s;
   const unsigned short* gl;
-  int lo;
   int hbase;
+  int sel_lo, sel_hi;
+  unsigned M;
   __device__ __forceinline__ unsigned lookup(int b) const {
-    const int i = b - lo;
-    if ((unsigned)i < (unsigned)RW_BINS) return s[i];
+    if (b < sel_lo || b > sel_hi) return M;
     return gl[b - hbase];
   }
 };
 
-// Index of one element from its bin code (§III.C): M unless binnable, in a selected bin, and the
-// error check passes. fast() never calls the exact float64 sequences: it returns UNDECIDED for
-// the rare points whose bin code lies outside the code window or whose check the float32
-// estimate cannot decide; exact() settles those afterwards.
-constexpr unsigned UNDECIDED = 0x10000u;   // above every index (indices are < 2^16)
-
+// Index of a point whose code is CODE_FAR (binnable, bin outside K1's code window): classify
+// it again with the exact sequences, look up its bin's rank, run the error-bound check (§III.C).
+// Every other point's index follows from its code alone.
 template <typename T>
-struct Assigner;
+struct FarAssigner;
 
 template <>
-struct Assigner<float> {
-  __device__ __forceinline__ static unsigned fast(float p, float x, unsigned code, int cbase,
-                                                  const Consts<float>& c, const RankView& rv,
-                                                  const float* s_m, const float*,
-                                                  const float* g_m, const float*, unsigned M) {
-    if (code == CODE_NONE) return M;
-    if (code == CODE_FAR) return UNDECIDED;
-    const unsigned r = rv.lookup(cbase + (int)code);
-    if (r == M) return M;
-    const float m = r < (unsigned)MT_SMEM ? s_m[r] : g_m[r];
-    return check_exact<float>(p, x, m, c.E_T) ? r : M;
-  }
-  __device__ static unsigned exact(float p, float x, unsigned code, int cbase,
-                                   const Consts<float>& c, const RankView& rv, const float* g_m,
-                                   const float*, unsigned M) {
-    if (code == CODE_NONE) return M;
-    int b = cbase + (int)code;
-    if (code == CODE_FAR && !classify_exact<float>(p, x, c, b)) return M;
+struct FarAssigner<float> {
+  __device__ __noinline__ static unsigned index(float p, float x, const Consts<float>& c,
+                                                const RankView& rv,
+                                   const float* g_m, const float*, unsigned M) {
+    int b = 0;
+    if (!classify_exact<float>(p, x, c, b)) return M;
     const unsigned r = rv.lookup(b);
     if (r == M) return M;
     return check_exact<float>(p, x, g_m[r], c.E_T) ? r : M;
@@ -78,26 +67,12 @@ struct Assigner<float> {
 };
 
 template <>
-struct Assigner<double> {
-  __device__ __forceinline__ static unsigned fast(double p, double x, unsigned code, int cbase,
-                                                  const Consts<double>& c, const RankView& rv,
-                                                  const double* s_m, const float* s_cf,
-                                                  const double* g_m, const float* g_cf,
-                                                  unsigned M) {
-    if (code == CODE_NONE) return M;
-    if (code == CODE_FAR) return UNDECIDED;
-    const unsigned r = rv.lookup(cbase + (int)code);
-    if (r == M) return M;
-    const float cf = r < (unsigned)MT_SMEM ? s_cf[r] : g_cf[r];
-    const int d = check_f64_fast(p, x, cf, c);
-    return d == 1 ? r : (d == 0 ? M : UNDECIDED);
-  }
-  __device__ static unsigned exact(double p, double x, unsigned code, int cbase,
-                                   const Consts<double>& c, const RankView& rv, const double* g_m,
-                                   const float* g_cf, unsigned M) {
-    if (code == CODE_NONE) return M;
-    int b = cbase + (int)code;
-    if (code == CODE_FAR && !classify_f64(p, x, c, b)) return M;
+struct FarAssigner<double> {
+  __device__ __noinline__ static unsigned index(double p, double x, const Consts<double>& c,
+                                   const RankView& rv, const double* g_m, const float* g_cf,
+                                   unsigned M) {
+    int b = 0;
+    if (!classify_f64(p, x, c, b)) return M;
     const unsigned r = rv.lookup(b);
     if (r == M) return M;
     return check_f64(p, x, g_m[r], g_cf[r], c) ? r : M;
@@ -122,153 +97,221 @@ struct Bits<double> {
 
 constexpr int K3_WARPS = 16;                    // warps per CTA; each warp owns whole tiles
 constexpr int K3_THREADS = K3_WARPS * 32;
-constexpr int K3_CHUNK = 1024;                  // elements a warp indexes before packing them
-constexpr int K3_UNROLL = 4;                    // 32-element steps whose loads are in flight
-constexpr int K3_WARP_SMEM = K3_CHUNK * 2;      // per-warp index buffer (bytes)
-constexpr int STEPS = SUB / 32;                 // 32-element steps (= ballot words) per tile
+constexpr int K3_SEG = 128;                     // elements per warp step: 4 consecutive per lane
+constexpr int K3_UNROLL = 4;                    // steps whose code loads are in flight together
+constexpr int STEPS = SUB / 32;                 // 32-element ballot words per tile
+constexpr int K3_SMEM = (CODE_BINS + 1) * 2;    // code-bin rank table (bytes)
 
-// K3a — indexing and packing. One warp processes one 4096-element tile at a time (tile
-// gw, gw + W, ... for global warp gw of W): for each 1024-element chunk it indexes every
-// element from K1's bin code (coalesced loads of code, p, x; lane l takes every 32nd element),
-// keeps the chunk's indices in its shared buffer and bit-packs them into the index block. It
-// records which points are incompressible as 16-bit half-ballots (half h of 32-element step s at
-// u16 index 2s + h of the tile's own codes, which the tile has already consumed: 4s + 2h < cnt/8
-// bytes < 2 cnt bytes), and the tile's incompressible count in the workspace. There is no
-// dependency between tiles and no block-wide barrier after the table set-up.
+// K3a — indexing and packing, from K1's codes alone. One warp processes one 4096-element tile at
+// a time (tile gw, gw + W, ... for global warp gw of W), in 128-element steps where lane l holds
+// elements 4l .. 4l+3: index = rank of the code's bin if the code says the point passed the
+// check of §III.C and the bin is selected, else the marker M (points with CODE_FAR are settled
+// from prev and cur). The lane's four B-bit indices form a 4B-bit field at bit 4Bl of the step's
+// image. When 4B is a multiple of 32 the lane stores its own words; otherwise output word w of
+// the image is assembled by lane w (and w - 32) from the fields that overlap it with warp
+// shuffles. Either way every store is coalesced (LSB-first order of §IV.C, zero padding to 16
+// bytes). The incompressible flags of each 32-element group go out as two 16-bit half-ballots
+// over the tile's own, already consumed codes (group s at u16 2s, 2s+1: 4s + 2 < 32 s + 32), and
+// the tile's count of incompressible points to the workspace. Tiles do not depend on each other
+// and there is no block-wide barrier after the rank table set-up. B is a template parameter so
+// that the packing is resolved at compile time.
+template <int B>
+struct Field {
+  using type = typename std::conditional<(4 * B <= 32), unsigned, unsigned long long>::type;
+};
+
+constexpr unsigned long long K3_FAR_FLAG = 1ull << 63;   // tile count word: far points pending
+
+// Output of one 128-element step whose lane l holds the indices of elements e0 = sb0 + 4l ..
+// e0 + 3 of the tile: incompressible flags as half-ballots, the packed B-bit fields, and the
+// step's incompressible count added to `count` (group leaders only).
+template <int B>
+__device__ __forceinline__ void step_out(const unsigned (&idx)[4], int sb0, int cnt, int lane,
+                                         unsigned short* halves, unsigned* tw, int twords,
+                                         int& count) {
+  using F = typename Field<B>::type;
+  constexpr int FB = 4 * B;
+  constexpr unsigned M = (1u << B) - 1u;
+  const int e0 = sb0 + lane * 4;
+  unsigned nib = 0;
+  F field = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    nib |= idx[k] == M ? (1u << k) : 0u;
+    field |= (F)idx[k] << (k * B);
+  }
+  if (sb0 + K3_SEG > cnt) {                      // last, partial step: drop points past cnt
+    const int nv = min(max(cnt - e0, 0), 4);
+    nib &= (1u << nv) - 1u;
+    field &= nv == 4 ? ~(F)0 : (((F)1 << (nv * B)) - 1);
+  }
+  // incompressible flags of the step's four 32-element groups (8 lanes each)
+  unsigned sb = nib << (4 * (lane & 7));
+  sb |= __shfl_xor_sync(0xffffffffu, sb, 1);
+  sb |= __shfl_xor_sync(0xffffffffu, sb, 2);
+  sb |= __shfl_xor_sync(0xffffffffu, sb, 4);
+  if ((lane & 7) == 0) {
+    const int st = (sb0 >> 5) + (lane >> 3);
+    if (st * 32 < cnt) halves[2 * st] = (unsigned short)(sb & 0xFFFFu);
+    if (st * 32 + 16 < cnt) halves[2 * st + 1] = (unsigned short)(sb >> 16);
+    count += __popc(sb);
+  }
+  const int wbase = (sb0 / K3_SEG) * FB;         // first word of the step in the tile image
+  if constexpr (FB == 32) {
+    if (wbase + lane < twords) tw[wbase + lane] = (unsigned)field;
+  } else if constexpr (FB == 64) {
+    const int w = wbase + 2 * lane;              // twords is even: both words or neither
+    if (w < twords)
+      *reinterpret_cast<uint2*>(tw + w) = make_uint2((unsigned)field, (unsigned)(field >> 32));
+  } else {
+    // word w of the step image takes the fields of lanes l0 .. l0 + KMAX - 1
+    constexpr int KMAX = 31 / FB + 2;
+    constexpr int RW = (FB + 31) / 32;
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+      const int w = lane + 32 * r;
+      const int bit = w * 32;
+      const int l0 = bit / FB;
+      unsigned acc = 0;
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k) {
+        const int l = l0 + k;
+        const F f = __shfl_sync(0xffffffffu, field, l & 31);
+        const int sh = l * FB - bit;             // start of lane l's field relative to the word
+        if (l < 32 && sh < 32) acc |= sh >= 0 ? (unsigned)(f << sh) : (unsigned)(f >> -sh);
+      }
+      if (w < FB && wbase + w < twords) tw[wbase + w] = acc;
+    }
+  }
+}
+
+// Geometry of tile gt: first element, element count, packed image and code area.
+struct TileRef {
+  long long j0;
+  int cnt, twords;
+  unsigned* tw;
+  unsigned short* halves;
+};
+template <int B>
+__device__ __forceinline__ TileRef tile_ref(const Geometry& g, long long gt, unsigned char* blob,
+                                            const unsigned short* codes) {
+  TileRef r;
+  const long long q = gt / g.spb, t = gt - q * g.spb;
+  r.j0 = q * g.epb + t * SUB;
+  const long long bend = min((long long)g.n, (long long)((q + 1) * g.epb));
+  r.cnt = (int)min((long long)SUB, bend - r.j0);
+  r.tw = reinterpret_cast<unsigned*>(blob + g.off_index + q * g.block_stride +
+                                     t * (long long)(SUB / 8 * B));
+  r.twords = 4 * ((r.cnt * B + 127) / 128);      // words of the 16-byte padded image
+  r.halves = const_cast<unsigned short*>(codes) + r.j0;
+  return r;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(K3_THREADS, 2) k3_assign(AssignArgs<T> A) {
-  __shared__ unsigned short s_rank[RW_BINS];
-  __shared__ T s_m[MT_SMEM];
-  __shared__ float s_cf[MT_SMEM];
-  extern __shared__ __align__(16) unsigned short k3_idx[];   // [K3_WARPS][K3_CHUNK]
-
-  const Geometry& g = A.g;
-  Ctrl* ctrl = A.ctrl;
-  const int tid = (int)threadIdx.x;
-  const int lane = (int)lane_id();
-  const int warp = tid >> 5;
-  const unsigned M = (unsigned)g.M;
-  Consts<T> c = A.c;
+__device__ __forceinline__ void anchor_consts(Consts<T>& c, const Geometry& g, const Ctrl* ctrl) {
   if (g.anchor == NUMARCK_ANCHOR_MIN) {
     c.a = (T)ctrl->a;
     c.af = (float)c.a;
     c.K0 = __fadd_ru(__fmul_ru(__fmul_ru(0x1p-18f, c.inv_wf), fabsf(c.af)), 0x1p-60f);
   }
+}
+
+template <typename T, int B>
+__global__ void __launch_bounds__(K3_THREADS, 2) k3_assign(AssignArgs<T> A) {
+  constexpr unsigned M = (1u << B) - 1u;
+  extern __shared__ unsigned short s_tab[];     // [CODE_BINS + 1]: rank of code bin i, or M
+
+  const Geometry& g = A.g;
+  const Ctrl* ctrl = A.ctrl;
+  const int tid = (int)threadIdx.x;
+  const int lane = (int)lane_id();
   const int any = ctrl->any;
-  const int bmin = ctrl->sel_bmin, bmax = ctrl->sel_bmax, n_sel = ctrl->n_sel;
   const int cbase = ctrl->code_base;
+  const int slo = any ? ctrl->sel_lo : 1, shi = any ? ctrl->sel_hi : 0;
 
-  // shared rank window: the whole bin range if it fits, else centred on the zero-change bin
-  int rwlo = bmin;
-  if (any && bmax - bmin + 1 > RW_BINS) {
-    const int c0 = cbase + CODE_HALF;
-    rwlo = min(max(c0 - RW_BINS / 2, bmin), bmax - RW_BINS + 1);
+  // rank of every bin of the code window (entry CODE_BINS, reached by CODE_NONE and CODE_FAR,
+  // is M); bins outside the selected range are M without a lookup
+  for (int i = tid; i <= CODE_BINS; i += K3_THREADS) {
+    const int b = cbase + i;
+    s_tab[i] = (i < CODE_BINS && b >= slo && b <= shi) ? A.rank_of[b - A.c.hbase]
+                                                        : (unsigned short)M;
   }
-  for (int i = tid; i < RW_BINS; i += K3_THREADS) {
-    const int b = rwlo + i;
-    s_rank[i] = (any && b <= bmax) ? A.rank_of[b - c.hbase] : (unsigned short)M;
-  }
-  const int nm = min(n_sel, MT_SMEM);
-  for (int r = tid; r < nm; r += K3_THREADS) {
-    s_m[r] = A.mtab[r];
-    s_cf[r] = A.cftab[r];
-  }
-  __syncthreads();   // the only block-wide barrier: tables are read-only from here on
-  const RankView rv{s_rank, A.rank_of, rwlo, c.hbase};
+  __syncthreads();   // the only block-wide barrier: the table is read-only from here on
 
-  const int B = g.B;
-  unsigned short* my_idx = k3_idx + warp * K3_CHUNK;
   const long long W = (long long)gridDim.x * K3_WARPS;
-  for (long long gt = (long long)blockIdx.x * K3_WARPS + warp; gt < g.nsub; gt += W) {
-    const long long q = gt / g.spb, t = gt - q * g.spb;
-    const long long j0 = q * g.epb + t * SUB;
-    const long long bend = min((long long)g.n, (long long)((q + 1) * g.epb));
-    const int cnt = (int)min((long long)SUB, bend - j0);
-    const T* pt = A.prev + j0;
-    const T* xt = A.cur + j0;
-    const unsigned short* ct = A.codes + j0;
-    unsigned short* halves = const_cast<unsigned short*>(A.codes) + j0;
-    unsigned char* tile_out = A.blob + g.off_index + q * g.block_stride + t * (long long)(SUB / 8 * B);
-
+  for (long long gt = (long long)blockIdx.x * K3_WARPS + (tid >> 5); gt < g.nsub; gt += W) {
+    const TileRef tr = tile_ref<B>(g, gt, A.blob, A.codes);
+    const int cnt = tr.cnt;
+    const unsigned short* ct = A.codes + tr.j0;
+    const bool al = (tr.j0 & 3) == 0;           // codes of the tile 8-byte aligned
     int count = 0;
-    for (int c0 = 0; c0 < cnt; c0 += K3_CHUNK) {
-      const int ccnt = min(K3_CHUNK, cnt - c0);
-      unsigned my_ball = 0;   // lane l: incompressible ballot of step l of the chunk
-      unsigned my_und = 0;    // lane l: undecided ballot of step l of the chunk
-      for (int i0 = 0; i0 < K3_CHUNK / 32; i0 += K3_UNROLL) {
-        T pv[K3_UNROLL], xv[K3_UNROLL];
-        unsigned cv[K3_UNROLL];
+    unsigned far = 0;                            // CODE_FAR seen (indexed as M for now)
+    for (int s0 = 0; s0 < cnt; s0 += K3_SEG * K3_UNROLL) {
+      uint2 cd[K3_UNROLL];   // four 16-bit codes per lane and step
 #pragma unroll
-        for (int u = 0; u < K3_UNROLL; ++u) {
-          const int e = (i0 + u) * 32 + lane;
-          pv[u] = (T)0;
-          xv[u] = (T)0;
-          cv[u] = CODE_NONE;
-          if (e < ccnt) {
-            cv[u] = __ldcs(ct + c0 + e);
-            pv[u] = ld_stream(pt + c0 + e);
-            xv[u] = ld_stream(xt + c0 + e);
-          }
-        }
+      for (int u = 0; u < K3_UNROLL; ++u) {
+        const int e0 = s0 + u * K3_SEG + lane * 4;
+        if (al && e0 + 4 <= cnt) {
+          cd[u] = __ldcs(reinterpret_cast<const uint2*>(ct + e0));
+        } else {
+          unsigned v[4];
 #pragma unroll
-        for (int u = 0; u < K3_UNROLL; ++u) {
-          const int e = (i0 + u) * 32 + lane;
-          unsigned idx = M;
-          if (any) idx = Assigner<T>::fast(pv[u], xv[u], cv[u], cbase, c, rv, s_m, s_cf, A.mtab,
-                                           A.cftab, M);
-          const bool und = e < ccnt && idx == UNDECIDED;
-          my_idx[e] = (unsigned short)(und ? 0u : idx);
-          const unsigned ball = __ballot_sync(0xffffffffu, e < ccnt && idx == M);
-          const unsigned uball = __ballot_sync(0xffffffffu, und);
-          if (lane == i0 + u) { my_ball = ball; my_und = uball; }
-          count += __popc(ball);
+          for (int k = 0; k < 4; ++k) v[k] = e0 + k < cnt ? (unsigned)ct[e0 + k] : CODE_NONE;
+          cd[u] = make_uint2(v[0] | (v[1] << 16), v[2] | (v[3] << 16));
         }
       }
-      // settle the undecided points exactly (rare): reload them, decide, patch the ballots
-      unsigned pending = __ballot_sync(0xffffffffu, my_und != 0u);
-      while (pending) {
-        const int st = __ffs(pending) - 1;
-        pending &= pending - 1;
-        const unsigned u = __shfl_sync(0xffffffffu, my_und, st);
-        bool mk = false;
-        if ((u >> lane) & 1u) {
-          const int e = st * 32 + lane;
-          const unsigned idx = Assigner<T>::exact(pt[c0 + e], xt[c0 + e], ct[c0 + e], cbase, c,
-                                                  rv, A.mtab, A.cftab, M);
-          my_idx[e] = (unsigned short)idx;
-          mk = idx == M;
+#pragma unroll
+      for (int u = 0; u < K3_UNROLL; ++u) {
+        const int sb0 = s0 + u * K3_SEG;
+        if (sb0 >= cnt) break;                   // uniform across the warp
+        unsigned idx[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const unsigned cv = ((k < 2 ? cd[u].x : cd[u].y) >> (16 * (k & 1))) & 0xFFFFu;
+          const unsigned r = s_tab[cv >> 1];
+          idx[k] = (cv & 1u) ? r : M;            // pass bit clear (or CODE_NONE): marker
+          far |= cv == CODE_FAR ? 1u : 0u;
         }
-        const unsigned fix = __ballot_sync(0xffffffffu, mk);
-        if (lane == st) my_ball |= fix;
-        count += __popc(fix);
+        step_out<B>(idx, sb0, cnt, lane, tr.halves, tr.tw, tr.twords, count);
       }
-      __syncwarp();
-      // the chunk's ballots, as 16-bit halves over the tile's consumed codes
-      {
-        const int s0 = (c0 >> 5) + lane;     // step of this lane's ballot
-        if (s0 * 32 < cnt) halves[2 * s0] = (unsigned short)(my_ball & 0xFFFFu);
-        if (s0 * 32 + 16 < cnt) halves[2 * s0 + 1] = (unsigned short)(my_ball >> 16);
-      }
-      // bit-pack the chunk: index e at bits [e*B, e*B + B) of the tile, LSB first; the image
-      // of the tile is padded with zero bytes to a multiple of 16. floor(v / B) for v < 2^15
-      // is (v * ceil(2^20 / B)) >> 20 exactly (the error stays below 1/32 < 1 - (B-1)/B).
-      const int nwords = ((((ccnt * B + 7) >> 3) + 15) >> 4) * 4;
-      unsigned* out = reinterpret_cast<unsigned*>(tile_out + (long long)(c0 / 8) * B);
-      const unsigned rB = ((1u << 20) + (unsigned)B - 1u) / (unsigned)B;
-      for (int w = lane; w < nwords; w += 32) {
-        const unsigned bit0 = (unsigned)w * 32u;
-        int e = (int)(((unsigned long long)bit0 * rB) >> 20);
-        const int e_end = min((int)(((unsigned long long)(bit0 + 31u) * rB) >> 20), ccnt - 1);
-        unsigned acc = 0;
-        for (; e <= e_end; ++e) {
-          const int sh = e * B - (int)bit0;
-          const unsigned xx = my_idx[e];
-          acc |= sh >= 0 ? (xx << sh) : (xx >> (-sh));
-        }
-        out[w] = acc;
-      }
-      __syncwarp();
     }
+    count = __reduce_add_sync(0xffffffffu, count);
+    const bool fix = any && __any_sync(0xffffffffu, far != 0u);
+    if (lane == 0) A.tstatus[gt] = (unsigned long long)count | (fix ? K3_FAR_FLAG : 0ull);
+  }
+}
+
+// K3f — tiles with points outside K1's code window (flagged by K3a; rare: a bin more than 16383
+// bins from the zero-change bin). Each such tile is indexed again from prev and cur with the
+// exact sequences (bin, rank, check of §III.C against the selected centre), replacing K3a's
+// image, ballots and count. The tile's codes are not used (K3a has written ballots over them).
+template <typename T, int B>
+__global__ void __launch_bounds__(K3_THREADS) k3_fixup(AssignArgs<T> A) {
+  constexpr unsigned M = (1u << B) - 1u;
+  const Geometry& g = A.g;
+  const Ctrl* ctrl = A.ctrl;
+  const int lane = (int)lane_id();
+  Consts<T> c = A.c;
+  anchor_consts<T>(c, g, ctrl);
+  const RankView rv{A.rank_of, c.hbase, ctrl->sel_lo, ctrl->sel_hi, M};
+  const long long W = (long long)gridDim.x * K3_WARPS;
+  for (long long gt = (long long)blockIdx.x * K3_WARPS + (threadIdx.x >> 5); gt < g.nsub;
+       gt += W) {
+    if (!(A.tstatus[gt] & K3_FAR_FLAG)) continue;   // uniform across the warp
+    const TileRef tr = tile_ref<B>(g, gt, A.blob, A.codes);
+    int count = 0;
+    for (int sb0 = 0; sb0 < tr.cnt; sb0 += K3_SEG) {
+      unsigned idx[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int e = sb0 + lane * 4 + k;
+        const long long j = tr.j0 + e;
+        idx[k] = e < tr.cnt ? FarAssigner<T>::index(A.prev[j], A.cur[j], c, rv, A.mtab, A.cftab, M)
+                            : M;
+      }
+      step_out<B>(idx, sb0, tr.cnt, lane, tr.halves, tr.tw, tr.twords, count);
+    }
+    count = __reduce_add_sync(0xffffffffu, count);
     if (lane == 0) A.tstatus[gt] = (unsigned long long)count;
   }
 }
@@ -380,59 +423,126 @@ __global__ void __launch_bounds__(SC_THREADS, 1) k3_scan(const unsigned long lon
   }
 }
 
-// K3c — incompressible values (§III.C): each warp takes a tile, reads all of its half-ballots
-// (before writing anything: the tile's own values may land on them) and its offset, then copies
-// the cur values of its incompressible points, in element order, into the incompressible table
-// (bit copies; only the sectors that hold those points are read).
+// K3c — incompressible values (§III.C). Each warp takes a tile: it gets the tile's marker flags
+// as 32-bit ballots (one per 32-element step), compacts the positions of the set bits into a
+// per-warp list in shared memory (popcounts and a warp scan give each step its place), then
+// copies the cur values at those positions into the incompressible table from the tile's entry
+// in the sub-block offset table, 32 independent loads per instruction and coalesced stores.
+//
+// The ballots come from the half-ballots that K3a left in the tile's code area, except when the
+// table can reach the code area (off_exact + n_inc * L > code offset, i.e. roughly more than 75%
+// (f64) or 50% (f32) of the points are incompressible): then a later tile's values may overwrite
+// an earlier tile's half-ballots before that tile has read them, so the flags are re-derived
+// from the packed indices (marker = 2^B - 1), which lie in a region no kernel writes after K3a.
+constexpr int K3X_WARPS = 8;
+constexpr int K3X_THREADS = K3X_WARPS * 32;
+constexpr int K3X_UNROLL = 4;
+constexpr int K3X_SMEM = K3X_WARPS * SUB * 2;   // per warp: up to SUB u16 positions
+
 template <typename T>
-__global__ void __launch_bounds__(512) k3_exact(const T* __restrict__ cur,
-                                                const unsigned short* codes, Geometry g,
-                                                unsigned char* blob) {
+__global__ void __launch_bounds__(K3X_THREADS) k3_exact(const T* __restrict__ cur,
+                                                        const unsigned short* codes, Geometry g,
+                                                        unsigned char* blob) {
+  extern __shared__ __align__(16) unsigned short k3x_list[];
   using U = typename Bits<T>::U;
   const int lane = (int)lane_id();
-  const long long W = (long long)gridDim.x * (blockDim.x >> 5);
+  unsigned short* list = k3x_list + (threadIdx.x >> 5) * SUB;
+  const long long W = (long long)gridDim.x * K3X_WARPS;
   U* exact_u = reinterpret_cast<U*>(blob + g.off_exact);
   const int64_t* sub_off = reinterpret_cast<const int64_t*>(blob + g.off_sub_off);
   const U* xu = reinterpret_cast<const U*>(cur);
-  for (long long gt = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); gt < g.nsub;
+  const long long L = (long long)sizeof(T);
+  const long long n_inc = reinterpret_cast<const numarck_header*>(blob)->n_inc;
+  const bool from_codes = g.off_exact + n_inc * L <= code_offset(g);
+  const int B = g.B;
+  const unsigned M = (unsigned)g.M, fmask = (1u << B) - 1u;
+  for (long long gt = (long long)blockIdx.x * K3X_WARPS + (threadIdx.x >> 5); gt < g.nsub;
        gt += W) {
     const long long q = gt / g.spb, t = gt - q * g.spb;
     const long long j0 = q * g.epb + t * SUB;
     const long long bend = min((long long)g.n, (long long)((q + 1) * g.epb));
     const int cnt = (int)min((long long)SUB, bend - j0);
-    const unsigned short* halves = codes + j0;
-    // lane l holds the ballots of steps l, l+32, l+64, l+96
+    // lane l holds the ballots of steps l, l+32, l+64, l+96 (all read before any store)
     unsigned mine[STEPS / 32];
+    if (from_codes) {
+      const unsigned short* halves = codes + j0;
+#pragma unroll
+      for (int k = 0; k < STEPS / 32; ++k) {
+        const int st = k * 32 + lane;
+        const unsigned lo = st * 32 < cnt ? halves[2 * st] : 0u;
+        const unsigned hi = st * 32 + 16 < cnt ? halves[2 * st + 1] : 0u;
+        mine[k] = lo | (hi << 16);
+      }
+    } else {
+      const unsigned* iw = reinterpret_cast<const unsigned*>(
+          blob + g.off_index + q * g.block_stride + t * (long long)(SUB / 8 * B));
+      // ballots staged in the last STEPS words of the list, read back before it is filled
+      unsigned* staged = reinterpret_cast<unsigned*>(list + SUB) - STEPS;
+#pragma unroll 4
+      for (int st = 0; st < STEPS; ++st) {
+        const int e = st * 32 + lane;
+        bool mk = false;
+        if (e < cnt) {
+          const unsigned bp = (unsigned)e * (unsigned)B;
+          const unsigned w = bp >> 5, o = bp & 31u;
+          unsigned long long v = iw[w];
+          if (o + (unsigned)B > 32u) v |= (unsigned long long)iw[w + 1] << 32;
+          mk = ((unsigned)(v >> o) & fmask) == M;
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, mk);
+        if (lane == 0) staged[st] = b;
+      }
+      __syncwarp();
+#pragma unroll
+      for (int k = 0; k < STEPS / 32; ++k) mine[k] = staged[k * 32 + lane];
+      __syncwarp();
+    }
+    // compact the marker positions of the tile, in element order
+    int total = 0;
 #pragma unroll
     for (int k = 0; k < STEPS / 32; ++k) {
-      const int st = k * 32 + lane;
-      const unsigned lo = st * 32 < cnt ? halves[2 * st] : 0u;
-      const unsigned hi = st * 32 + 16 < cnt ? halves[2 * st + 1] : 0u;
-      mine[k] = lo | (hi << 16);
+      const int c = __popc(mine[k]);
+      const int incl = warp_incl_scan(c);
+      int p = total + incl - c;
+      unsigned m = mine[k];
+      const int e0 = (k * 32 + lane) * 32;
+      while (m) {
+        const int bit = __ffs(m) - 1;
+        m &= m - 1u;
+        list[p++] = (unsigned short)(e0 + bit);
+      }
+      total += __shfl_sync(0xffffffffu, incl, 31);
     }
     __syncwarp();
-    long long run = sub_off[gt];
-    // steps in groups of 8: the gathers of a group are in flight together before its stores
+    const U* src = xu + j0;
+    U* dst = exact_u + sub_off[gt];
+    for (int i0 = 0; i0 < total; i0 += 32 * K3X_UNROLL) {
+      U v[K3X_UNROLL];
 #pragma unroll
-    for (int k = 0; k < STEPS / 32; ++k) {
+      for (int u = 0; u < K3X_UNROLL; ++u) {
+        const int i = i0 + u * 32 + lane;
+        v[u] = i < total ? src[list[i]] : (U)0;
+      }
 #pragma unroll
-      for (int s0 = 0; s0 < 32; s0 += 8) {
-        unsigned ball[8];
-        U val[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          ball[u] = __shfl_sync(0xffffffffu, mine[k], s0 + u);
-          val[u] = 0;
-          if ((ball[u] >> lane) & 1u) val[u] = xu[j0 + (long long)(k * 32 + s0 + u) * 32 + lane];
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          if ((ball[u] >> lane) & 1u) exact_u[run + __popc(ball[u] & lanemask_lt())] = val[u];
-          run += __popc(ball[u]);
-        }
+      for (int u = 0; u < K3X_UNROLL; ++u) {
+        const int i = i0 + u * 32 + lane;
+        if (i < total) dst[i] = v[u];
       }
     }
+    __syncwarp();   // the list is rebuilt for the next tile
   }
+}
+
+template <typename T>
+using K3Fn = void (*)(AssignArgs<T>);
+
+template <typename T, int... Bs>
+constexpr std::array<K3Fn<T>, sizeof...(Bs)> k3_table(std::integer_sequence<int, Bs...>) {
+  return {{&k3_assign<T, Bs + 1>...}};
+}
+template <typename T, int... Bs>
+constexpr std::array<K3Fn<T>, sizeof...(Bs)> k3f_table(std::integer_sequence<int, Bs...>) {
+  return {{&k3_fixup<T, Bs + 1>...}};
 }
 
 }  // namespace
@@ -452,24 +562,34 @@ static cudaError_t launch_assign_t(const CompressPlan& P, cudaStream_t s, const 
   A.tstatus = reinterpret_cast<unsigned long long*>(P.ws + P.wl.status);
   A.blob = P.blob;
   A.codes = reinterpret_cast<const unsigned short*>(P.blob + code_offset(P.g));
-  static int occ[64] = {0};
+  static const std::array<K3Fn<T>, NUMARCK_MAX_B> table =
+      k3_table<T>(std::make_integer_sequence<int, NUMARCK_MAX_B>{});
+  if (P.g.B < 1 || P.g.B > NUMARCK_MAX_B) return cudaErrorInvalidValue;
+  const K3Fn<T> fn = table[P.g.B - 1];
+  static int occ[64][NUMARCK_MAX_B + 1] = {};
   int dev = 0;
   cudaGetDevice(&dev);
-  int per_sm = dev < 64 ? occ[dev] : 0;
-  const int dyn = K3_WARPS * K3_WARP_SMEM;
+  int per_sm = dev < 64 ? occ[dev][P.g.B] : 0;
   if (per_sm == 0) {
-    cudaError_t e = cudaFuncSetAttribute(k3_assign<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         dyn);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, K3_SMEM);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_assign<T>, K3_THREADS, dyn);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, K3_THREADS, K3_SMEM);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    if (dev < 64) occ[dev] = per_sm;
+    if (dev < 64) occ[dev][P.g.B] = per_sm;
   }
   long long blocks = (long long)P.sms * per_sm;
   const long long need = (P.g.nsub + K3_WARPS - 1) / K3_WARPS;
   if (blocks > need) blocks = need;
-  k3_assign<T><<<(int)blocks, K3_THREADS, dyn, s>>>(A);
+  fn<<<(int)blocks, K3_THREADS, K3_SMEM, s>>>(A);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // K3f: tiles with points outside the code window (usually none; the kernel only reads flags)
+  static const std::array<K3Fn<T>, NUMARCK_MAX_B> fix_table =
+      k3f_table<T>(std::make_integer_sequence<int, NUMARCK_MAX_B>{});
+  long long fblocks = (long long)P.sms * 2;
+  if (fblocks > need) fblocks = need;
+  fix_table[P.g.B - 1]<<<(int)fblocks, K3_THREADS, 0, s>>>(A);
   return cudaGetLastError();
 }
 
@@ -483,16 +603,33 @@ cudaError_t launch_offsets(const CompressPlan& P, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <typename T>
+static cudaError_t launch_exact_t(const CompressPlan& P, cudaStream_t s) {
+  static int occ[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int per_sm = dev < 64 ? occ[dev] : 0;
+  if (per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k3_exact<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         K3X_SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_exact<T>, K3X_THREADS, K3X_SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (dev < 64) occ[dev] = per_sm;
+  }
+  long long blocks = (long long)P.sms * per_sm;
+  const long long need = (P.g.nsub + K3X_WARPS - 1) / K3X_WARPS;
+  if (blocks > need) blocks = need;
+  const unsigned short* codes = reinterpret_cast<const unsigned short*>(P.blob + code_offset(P.g));
+  k3_exact<T><<<(int)blocks, K3X_THREADS, K3X_SMEM, s>>>(static_cast<const T*>(P.cur), codes, P.g,
+                                                          P.blob);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_exact(const CompressPlan& P, cudaStream_t s) {
   if (P.g.nsub == 0) return cudaSuccess;
-  long long xb = (P.g.nsub + 15) / 16;
-  if (xb > (long long)P.sms * 4) xb = (long long)P.sms * 4;
-  const unsigned short* codes = reinterpret_cast<const unsigned short*>(P.blob + code_offset(P.g));
-  if (P.g.dtype == NUMARCK_F64)
-    k3_exact<double><<<(int)xb, 512, 0, s>>>(static_cast<const double*>(P.cur), codes, P.g, P.blob);
-  else
-    k3_exact<float><<<(int)xb, 512, 0, s>>>(static_cast<const float*>(P.cur), codes, P.g, P.blob);
-  return cudaGetLastError();
+  return P.g.dtype == NUMARCK_F64 ? launch_exact_t<double>(P, s) : launch_exact_t<float>(P, s);
 }
 
 cudaError_t launch_assign(const CompressPlan& P, cudaStream_t s) {

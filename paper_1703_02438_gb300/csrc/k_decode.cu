@@ -1,18 +1,24 @@
 // k_decode.cu — K4/K5: decompression (§III.E, Eq. 4 read as R = prev * (1 + centre)) and
 // partial decompression of a segment (§IV.C, §V.C).
 //
-// One tile = one 4096-element sub-block. A tile loads its packed index bits into shared memory,
-// unpacks B-bit fields, numbers its incompressible points in element order (warp ballots and a
-// scan over 32-element chunks) and takes their values from the incompressible table starting at
-// the sub-block's offset; every other point is prev * m[idx] with m = 1 + centre computed in T
-// once per CTA. Tiles are independent, so the kernel is a persistent grid with a static tile
-// stride. A segment decode touches only the tiles that overlap it (the paper decodes the index
-// blocks that cover the segment and finds its first incompressible value through the per-block
-// offset table; the per-sub-block table refines that to 4096 elements).
+// One warp decodes one 4096-element tile (sub-block) at a time, in 128-element steps where lane
+// l owns elements 4l .. 4l+3: it reads its 4B-bit field of the step's packed image (one word
+// when B = 8, two when B = 16, else the two or three words the field overlaps), splits it into
+// four indices, numbers the incompressible points of the step in element order with four
+// ballots from the tile's entry in the sub-block offset table, and writes prev * m[idx] or the
+// incompressible value; prev and R move as 16-byte vectors when the tile lies inside the
+// segment and both pointers are aligned. m = 1 + centre is computed in T once per CTA. Tiles
+// are independent, so the kernel is a persistent grid with a static tile stride. A segment
+// decode touches only the tiles that overlap it (the paper decodes the index blocks that cover
+// the segment and finds its first incompressible value through the per-block offset table; the
+// per-sub-block table refines that to 4096 elements). B, read from the header on the device, is
+// dispatched once per CTA to a body compiled for that width.
 //
 // The kernel reads the blob header from device memory and validates it (magic, version, status
 // word, geometry implied by n/B/block size, counts), so decompression needs no host round trip
 // after compression: a compress -> decompress chain stays asynchronous on one stream.
+#include <type_traits>
+
 #include "launch.h"
 
 namespace nmk {
@@ -32,48 +38,90 @@ struct BitsOf;
 template <>
 struct BitsOf<float> {
   using U = unsigned int;
+  __device__ __forceinline__ static float as(U u) { return __uint_as_float(u); }
 };
 template <>
 struct BitsOf<double> {
   using U = unsigned long long;
+  __device__ __forceinline__ static double as(U u) { return __longlong_as_double((long long)u); }
 };
+
+// Four consecutive T as 16-byte vectors (16-byte aligned addresses).
+__device__ __forceinline__ void ld4(const double* p, double* v) {
+  const double2 a = __ldcs(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldcs(reinterpret_cast<const double2*>(p) + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void ld4(const float* p, float* v) {
+  const float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void st4(double* p, const double* v) {
+  __stcs(reinterpret_cast<double2*>(p), make_double2(v[0], v[1]));
+  __stcs(reinterpret_cast<double2*>(p) + 1, make_double2(v[2], v[3]));
+}
+__device__ __forceinline__ void st4(float* p, const float* v) {
+  __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+}
 
 constexpr int K4_WARPS = 16;                    // warps per CTA (each owns whole tiles)
 constexpr int K4_THREADS = K4_WARPS * 32;
-constexpr int K4_CHUNK = 1024;                  // elements decoded per step of a warp
-constexpr int K4_UNROLL = 8;                    // 32-element steps whose loads are in flight
-constexpr int K4_WORDS = K4_CHUNK * NUMARCK_MAX_B / 32 + 8;   // packed words of a chunk (+guard)
-constexpr int K4_DYN_SMEM = DM_SMEM * 8 + K4_WARPS * K4_WORDS * 4;
+constexpr int K4_SEG = 128;                     // elements per warp step: 4 consecutive per lane
+constexpr int K4_UNROLL = 1;                    // steps whose loads are in flight together
 
-// One warp decodes one 4096-element tile at a time, in 1024-element chunks: it copies the
-// chunk's packed bits into its shared buffer, unpacks B-bit fields, and walks the chunk in
-// 32-element steps, numbering incompressible points with ballots from the tile's entry in the
-// sub-block offset table. No block-wide barrier is needed after the multiplier table is built.
-template <typename T>
+template <int B>
+struct Field {
+  using type = typename std::conditional<(4 * B <= 32), unsigned, unsigned long long>::type;
+};
+
+// The 4B-bit field of lane `lane` in the step whose image starts at word ws of the tile image
+// tw (twords words). Words past the image read as 0.
+template <int B>
+__device__ __forceinline__ typename Field<B>::type load_field(const unsigned* tw, int twords,
+                                                              int ws, int lane) {
+  constexpr int FB = 4 * B;
+  using F = typename Field<B>::type;
+  if constexpr (FB == 32) {
+    const int w = ws + lane;
+    return w < twords ? __ldg(tw + w) : 0u;
+  } else if constexpr (FB == 64) {
+    const int w = ws + 2 * lane;                 // twords is even: both words or neither
+    if (w >= twords) return 0ull;
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(tw + w));
+    return (unsigned long long)v.x | ((unsigned long long)v.y << 32);
+  } else {
+    const int bit = FB * lane;
+    const int w0 = ws + (bit >> 5), o = bit & 31;
+    const unsigned a0 = w0 < twords ? __ldg(tw + w0) : 0u;
+    const unsigned a1 = (o + FB > 32 && w0 + 1 < twords) ? __ldg(tw + w0 + 1) : 0u;
+    const unsigned long long v = (unsigned long long)a0 | ((unsigned long long)a1 << 32);
+    if constexpr (FB > 32) {
+      const unsigned a2 = (o + FB > 64 && w0 + 2 < twords) ? __ldg(tw + w0 + 2) : 0u;
+      return (F)((v >> o) | (o ? ((unsigned long long)a2 << (64 - o)) : 0ull));
+    } else {
+      return (F)(v >> o);
+    }
+  }
+}
+
+template <typename T, int B>
 __device__ __forceinline__ void decode_tiles(const DecodeArgs& A, const Geometry& g,
                                              long long n_inc, long long g0, long long g1,
-                                             unsigned char* dyn) {
-  const int tid = (int)threadIdx.x;
+                                             const T* s_m) {
+  using U = typename BitsOf<T>::U;
+  using F = typename Field<B>::type;
+  constexpr int FB = 4 * B;
+  constexpr unsigned M = (1u << B) - 1u;
   const int lane = (int)lane_id();
-  const int warp = tid >> 5;
-  const int B = g.B;
-  const unsigned M = (unsigned)g.M;
-  const unsigned mask = (1u << B) - 1u;
+  const int warp = (int)(threadIdx.x >> 5);
   const T* centres = reinterpret_cast<const T*>(A.blob + g.off_centres);
   const int64_t* idx_off = reinterpret_cast<const int64_t*>(A.blob + g.off_idx_off);
   const int64_t* sub_off = reinterpret_cast<const int64_t*>(A.blob + g.off_sub_off);
-  using U = typename BitsOf<T>::U;
   const U* exact_u = reinterpret_cast<const U*>(A.blob + g.off_exact);
   const unsigned char* index = A.blob + g.off_index;
   const T* prev = static_cast<const T*>(A.prev_seg);
   T* out = static_cast<T*>(A.out_seg);
-  U* out_u = reinterpret_cast<U*>(A.out_seg);
-  T* s_m = reinterpret_cast<T*>(dyn);
-  unsigned* words = reinterpret_cast<unsigned*>(dyn + DM_SMEM * 8) + warp * K4_WORDS;
-
-  const int nm = min(1 << B, DM_SMEM);
-  for (int r = tid; r < nm; r += K4_THREADS) s_m[r] = t_add((T)1, centres[r]);
-  __syncthreads();   // the only block-wide barrier
+  const unsigned lt = lanemask_lt();
 
   const long long seg_lo = A.start, seg_hi = A.start + A.count;
   const long long W = (long long)gridDim.x * K4_WARPS;
@@ -85,75 +133,106 @@ __device__ __forceinline__ void decode_tiles(const DecodeArgs& A, const Geometry
     const long long base = sub_off[gt];
     const long long boff = idx_off[q];
     const long long tstart = boff + t * (long long)(SUB / 8 * B);
-    const long long tend = tstart + 16LL * (((cnt * B + 7) / 8 + 15) / 16);
-    if (base < 0 || base > n_inc || (boff & 15) || boff < 0 || tend > g.index_bytes) {
+    const int twords = 4 * ((cnt * B + 127) / 128);
+    if (base < 0 || base > n_inc || (boff & 15) || boff < 0 ||
+        tstart + 4LL * twords > g.index_bytes) {
       if (lane == 0 && A.status) atomicExch(A.status, NUMARCK_ERR_CORRUPT);
       continue;
     }
+    const unsigned* tw = reinterpret_cast<const unsigned*>(index + tstart);
+    // elements [e_lo, e_hi) of the tile lie in the segment; pt/ot address tile element 0
+    const int e_lo = (int)max(0LL, seg_lo - j0);
+    const int e_hi = (int)min((long long)cnt, seg_hi - j0);
+    const T* pt = prev + (j0 - seg_lo);
+    T* ot = out + (j0 - seg_lo);
+    const bool vec = e_lo == 0 && ((reinterpret_cast<uintptr_t>(pt) |
+                                    reinterpret_cast<uintptr_t>(ot)) & 15) == 0;
     long long run = base;
-    bool whole = true;
-    for (int c0 = 0; c0 < cnt; c0 += K4_CHUNK) {
-      const long long cj = j0 + c0;
-      if (cj >= seg_hi) { whole = false; break; }
-      const int ccnt = min(K4_CHUNK, cnt - c0);
-      const int nv16 = (((ccnt * B + 7) >> 3) + 15) >> 4;
-      const uint4* src = reinterpret_cast<const uint4*>(index + tstart + (c0 / 8) * B);
-      for (int v = lane; v < nv16; v += 32) reinterpret_cast<uint4*>(words)[v] = __ldcs(src + v);
-      if (lane < 4) words[nv16 * 4 + lane] = 0u;
-      __syncwarp();
-      const bool emit = cj + ccnt > seg_lo;   // else: only count this chunk's markers
-      for (int i0 = 0; i0 < K4_CHUNK / 32; i0 += K4_UNROLL) {
-        T pv[K4_UNROLL];
+    for (int s0 = 0; s0 < e_hi; s0 += K4_SEG * K4_UNROLL) {
+      F field[K4_UNROLL];
+      T pv[K4_UNROLL][4];
 #pragma unroll
-        for (int u = 0; u < K4_UNROLL; ++u) {
-          const int e = (i0 + u) * 32 + lane;
-          const long long j = cj + e;
-          pv[u] = (emit && e < ccnt && j >= seg_lo && j < seg_hi) ? ld_stream(prev + (j - seg_lo))
-                                                                   : (T)0;
-        }
+      for (int u = 0; u < K4_UNROLL; ++u) {
+        const int sb0 = s0 + u * K4_SEG;
+        const int e0 = sb0 + 4 * lane;
+        field[u] = sb0 < e_hi ? load_field<B>(tw, twords, (sb0 / K4_SEG) * FB, lane) : (F)0;
+        if (vec && sb0 + K4_SEG <= e_hi) {
+          ld4(pt + e0, pv[u]);
+        } else {
 #pragma unroll
-        for (int u = 0; u < K4_UNROLL; ++u) {
-          const int e = (i0 + u) * 32 + lane;
-          unsigned id = 0;
-          if (e < ccnt) {
-            const unsigned bp = (unsigned)e * (unsigned)B;
-            const unsigned w = bp >> 5, o = bp & 31u;
-            const unsigned long long v2 =
-                ((unsigned long long)words[w + 1] << 32) | (unsigned long long)words[w];
-            id = (unsigned)(v2 >> o) & mask;
-          }
-          const bool mk = e < ccnt && id == M;
-          const unsigned ball = __ballot_sync(0xffffffffu, mk);
-          const long long j = cj + e;
-          if (emit && e < ccnt && j >= seg_lo && j < seg_hi) {
-            const long long o = j - seg_lo;
-            if (mk) {
-              const long long pos = run + __popc(ball & lanemask_lt());
-              if (pos < n_inc) {
-                out_u[o] = exact_u[pos];
-              } else {
-                out_u[o] = 0;
-                if (A.status) atomicExch(A.status, NUMARCK_ERR_CORRUPT);
-              }
-            } else {
-              const T m = id < (unsigned)DM_SMEM ? s_m[id] : t_add((T)1, centres[id]);
-              out[o] = t_mul(pv[u], m);
-            }
-          }
-          run += __popc(ball);
+          for (int k = 0; k < 4; ++k)
+            pv[u][k] = (e0 + k >= e_lo && e0 + k < e_hi) ? __ldcs(pt + e0 + k) : (T)0;
         }
       }
-      __syncwarp();
+#pragma unroll
+      for (int u = 0; u < K4_UNROLL; ++u) {
+        const int sb0 = s0 + u * K4_SEG;
+        if (sb0 >= e_hi) break;                  // uniform across the warp
+        const int e0 = sb0 + 4 * lane;
+        unsigned id[4];
+        unsigned nib = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          id[k] = (unsigned)(field[u] >> (k * B)) & M;
+          nib |= (e0 + k < cnt && id[k] == M) ? (1u << k) : 0u;
+        }
+        // element-order numbering of the step's incompressible points: lanes before this one,
+        // then this lane's earlier elements
+        unsigned before = 0, total = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const unsigned bk = __ballot_sync(0xffffffffu, (nib >> k) & 1u);
+          before += __popc(bk & lt);
+          total += __popc(bk);
+        }
+        T r[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if ((nib >> k) & 1u) {
+            const long long pos = run + before + __popc(nib & ((1u << k) - 1u));
+            U v = 0;
+            if (pos < n_inc) v = exact_u[pos];
+            else if (A.status && e0 + k >= e_lo && e0 + k < e_hi)
+              atomicExch(A.status, NUMARCK_ERR_CORRUPT);
+            r[k] = BitsOf<T>::as(v);
+          } else {
+            T m;
+            if constexpr ((1 << B) <= DM_SMEM) m = s_m[id[k]];
+            else m = id[k] < (unsigned)DM_SMEM ? s_m[id[k]] : t_add((T)1, centres[id[k]]);
+            r[k] = t_mul(pv[u][k], m);
+          }
+        }
+        run += total;
+        if (vec && sb0 + K4_SEG <= e_hi) {
+          st4(ot + e0, r);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (e0 + k >= e_lo && e0 + k < e_hi) ot[e0 + k] = r[k];
+        }
+      }
     }
-    if (whole && lane == 0 && A.status) {
+    if (e_hi == cnt && lane == 0 && A.status) {
       const long long next = (gt + 1 < g.nsub) ? sub_off[gt + 1] : n_inc;
       if (run != next) atomicExch(A.status, NUMARCK_ERR_CORRUPT);
     }
   }
 }
 
+template <typename T, int B = 1>
+__device__ __forceinline__ void decode_dispatch(const DecodeArgs& A, const Geometry& g,
+                                                long long n_inc, long long g0, long long g1,
+                                                const T* s_m) {
+  if constexpr (B <= NUMARCK_MAX_B) {
+    if (g.B == B)
+      decode_tiles<T, B>(A, g, n_inc, g0, g1, s_m);
+    else
+      decode_dispatch<T, B + 1>(A, g, n_inc, g0, g1, s_m);
+  }
+}
+
 __global__ void __launch_bounds__(K4_THREADS, 2) k4_decode(DecodeArgs A) {
-  extern __shared__ __align__(16) unsigned char k4_dyn[];
+  __shared__ __align__(16) unsigned char s_tab[DM_SMEM * 8];   // multipliers m = 1 + centre
   __shared__ __align__(16) numarck_header s_h;
   __shared__ Geometry s_g;
   __shared__ long long s_g0, s_g1;
@@ -185,10 +264,20 @@ __global__ void __launch_bounds__(K4_THREADS, 2) k4_decode(DecodeArgs A) {
   __syncthreads();
   if (!s_ok) return;
   const Geometry g = s_g;
-  if (g.dtype == NUMARCK_F64)
-    decode_tiles<double>(A, g, s_h.n_inc, s_g0, s_g1, k4_dyn);
-  else
-    decode_tiles<float>(A, g, s_h.n_inc, s_g0, s_g1, k4_dyn);
+  const int nm = min(1 << g.B, DM_SMEM);
+  if (g.dtype == NUMARCK_F64) {
+    double* s_m = reinterpret_cast<double*>(s_tab);
+    const double* centres = reinterpret_cast<const double*>(A.blob + g.off_centres);
+    for (int r = threadIdx.x; r < nm; r += K4_THREADS) s_m[r] = t_add(1.0, centres[r]);
+    __syncthreads();   // the only block-wide barrier after the header
+    decode_dispatch<double>(A, g, s_h.n_inc, s_g0, s_g1, s_m);
+  } else {
+    float* s_m = reinterpret_cast<float*>(s_tab);
+    const float* centres = reinterpret_cast<const float*>(A.blob + g.off_centres);
+    for (int r = threadIdx.x; r < nm; r += K4_THREADS) s_m[r] = t_add(1.0f, centres[r]);
+    __syncthreads();
+    decode_dispatch<float>(A, g, s_h.n_inc, s_g0, s_g1, s_m);
+  }
 }
 
 }  // namespace
@@ -200,10 +289,7 @@ cudaError_t launch_decode(const DecodePlan& P, cudaStream_t s) {
   cudaGetDevice(&dev);
   int per_sm = dev < 64 ? occ[dev] : 0;
   if (per_sm == 0) {
-    cudaError_t e = cudaFuncSetAttribute(k4_decode, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         K4_DYN_SMEM);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k4_decode, K4_THREADS, K4_DYN_SMEM);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k4_decode, K4_THREADS, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     if (dev < 64) occ[dev] = per_sm;
@@ -214,7 +300,7 @@ cudaError_t launch_decode(const DecodePlan& P, cudaStream_t s) {
     if (blocks > need) blocks = need;
   }
   DecodeArgs A{P.blob, P.prev_seg, P.out_seg, P.status, P.start, P.count, P.n_expected};
-  k4_decode<<<(int)blocks, K4_THREADS, K4_DYN_SMEM, s>>>(A);
+  k4_decode<<<(int)blocks, K4_THREADS, 0, s>>>(A);
   return cudaGetLastError();
 }
 

@@ -2,6 +2,11 @@
 // min/max of the change ratios); K1: change ratio (Eq. 1) -> bin id -> top-k histogram
 // (§IV.B.1), fused in one pass over both timesteps with 128-bit streaming loads.
 //
+// K1 also runs the error-bound check of §III.C for every binnable point against the centre of
+// its own bin (the only centre the point can be indexed to, whichever bins are selected) and
+// stores bin and outcome as a 16-bit code, so that the indexing kernel reads 2 bytes per point
+// instead of both timesteps.
+//
 // The paper builds a local histogram per MPI rank and merges them with MPI_Allreduce (§IV.B.1).
 // Here each CTA keeps a private shared-memory histogram over a 16384-bin window around the
 // zero-change bin; lanes of a warp that hit the same bin are merged with match.any before one
@@ -21,6 +26,7 @@ __device__ __forceinline__ void anchor_min_consts(Consts<T>& c, const Ctrl* ctrl
   c.a = (T)a;             // exact: the key was made from a T value
   c.af = (float)c.a;
   c.K0 = __fadd_ru(__fmul_ru(__fmul_ru(0x1p-18f, c.inv_wf), fabsf(c.af)), 0x1p-60f);
+  c.C0 = __fmaf_ru(0x1p-22f, fabsf(c.af), __fadd_ru(0x1.8p-49f, 0x1p-100f));
 }
 
 // ---------------------------------------------------------------------------------------
@@ -62,10 +68,10 @@ struct HistCtx {
   unsigned short* codes;      // per-element bin codes (scratch at the blob's tail)
 };
 
-__device__ __forceinline__ unsigned short bin_code(const HistCtx& h, bool binned, int b) {
-  if (!binned) return (unsigned short)CODE_NONE;
+__device__ __forceinline__ unsigned bin_code(const HistCtx& h, bool binned, int b, bool pass) {
+  if (!binned) return CODE_NONE;
   const unsigned off = (unsigned)(b - h.cbase);
-  return (unsigned short)(off < CODE_FAR ? off : CODE_FAR);
+  return off < (unsigned)CODE_BINS ? (off << 1) | (pass ? 1u : 0u) : CODE_FAR;
 }
 
 // All 32 lanes call this together (valid may differ per lane).
@@ -87,26 +93,46 @@ __device__ __forceinline__ void hist_add(const HistCtx& h, bool valid, int b) {
   }
 }
 
+// Exact bin and own-bin check (§III.B, §III.C) of one float64 point (the rare undecided points).
+static __device__ __noinline__ int classify_check_f64_slow(double p, double x,
+                                                           const Consts<double>& c, int cbase,
+                                                           int* b, bool* pass) {
+  int bb = 0;
+  const int k = classify_exact<double>(p, x, c, bb);
+  *b = bb;
+  *pass = k && (unsigned)(bb - cbase) < (unsigned)CODE_BINS &&
+          check_exact<double>(p, x, bin_multiplier<double>(bb, c.a, c.w), c.E_T);
+  return k;
+}
+
 template <typename T>
 struct Classifier;
 
-// fast(): 1 (binnable, bin in b), 0 (not binnable) or 2 (undecided: call exact()).
+// fast(): 0 (not binnable), 1 (bin in b; pass = the own-bin check when b is in the code window)
+// or 2/3 (undecided: call exact()). exact() decides both with the exact T sequences.
 template <>
 struct Classifier<float> {
-  __device__ __forceinline__ static int fast(float p, float x, const Consts<float>& c, int& b) {
-    return classify_exact<float>(p, x, c, b);
+  __device__ __forceinline__ static int fast(float p, float x, const Consts<float>& c, int cbase,
+                                             int& b, bool& pass) {
+    return exact(p, x, c, cbase, b, pass);
   }
-  __device__ static int exact(float p, float x, const Consts<float>& c, int& b) {
-    return classify_exact<float>(p, x, c, b);
+  __device__ __forceinline__ static int exact(float p, float x, const Consts<float>& c, int cbase,
+                                              int& b, bool& pass) {
+    const int k = classify_exact<float>(p, x, c, b);
+    pass = k && (unsigned)(b - cbase) < (unsigned)CODE_BINS &&
+           check_exact<float>(p, x, bin_multiplier<float>(b, c.a, c.w), c.E_T);
+    return k;
   }
 };
 template <>
 struct Classifier<double> {
-  __device__ __forceinline__ static int fast(double p, double x, const Consts<double>& c, int& b) {
-    return classify_f64_fast(p, x, c, b);
+  __device__ __forceinline__ static int fast(double p, double x, const Consts<double>& c,
+                                             int cbase, int& b, bool& pass) {
+    return classify_check_f64_fast(p, x, c, cbase, b, pass);
   }
-  __device__ static int exact(double p, double x, const Consts<double>& c, int& b) {
-    return classify_exact_f64_slow(p, x, c, &b);
+  __device__ static int exact(double p, double x, const Consts<double>& c, int cbase, int& b,
+                              bool& pass) {
+    return classify_check_f64_slow(p, x, c, cbase, &b, &pass);
   }
 };
 
@@ -115,18 +141,24 @@ struct Vec;
 template <>
 struct Vec<float> {
   using type = float4;
+  using codes = uint2;   // 4 codes
   static constexpr int N = 4;
   __device__ __forceinline__ static void get(const type& v, float* o) {
     o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+  __device__ __forceinline__ static codes pack(const unsigned* k) {
+    return make_uint2(k[0] | (k[1] << 16), k[2] | (k[3] << 16));
   }
 };
 template <>
 struct Vec<double> {
   using type = double2;
+  using codes = unsigned;   // 2 codes
   static constexpr int N = 2;
   __device__ __forceinline__ static void get(const type& v, double* o) {
     o[0] = v.x; o[1] = v.y;
   }
+  __device__ __forceinline__ static codes pack(const unsigned* k) { return k[0] | (k[1] << 16); }
 };
 
 constexpr int K1_THREADS = 512;
@@ -181,37 +213,35 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_hist(const T* __restrict__ p
         V::get(a, pe[u]);
         V::get(b, xe[u]);
       }
-      unsigned pend = 0;   // bit u * V::N + v: element needs the exact sequence
+      unsigned pend = 0;   // bit u * V::N + v: element needs the exact sequences
 #pragma unroll
       for (int u = 0; u < K1_UNROLL; ++u) {
         const int64_t vi = base + u * 32 + lane;
+        unsigned cw[V::N];
 #pragma unroll
         for (int v = 0; v < V::N; ++v) {
           int b = 0;
-          const int kind = ok[u] ? Classifier<T>::fast(pe[u][v], xe[u][v], c, b) : 0;
+          bool pass = false;
+          const int kind = ok[u] ? Classifier<T>::fast(pe[u][v], xe[u][v], c, h.cbase, b, pass) : 0;
           const bool binned = kind == 1;
           if (binned) { lmin = min(lmin, b); lmax = max(lmax, b); }
-          if (kind == 2) pend |= 1u << (u * V::N + v);
-          else if (ok[u]) codes[vi * V::N + v] = bin_code(h, binned, b);
+          if (kind >= 2) pend |= 1u << (u * V::N + v);
+          cw[v] = bin_code(h, binned, b, pass);
           hist_add(h, binned, b);
         }
+        if (ok[u]) reinterpret_cast<typename V::codes*>(codes)[vi] = V::pack(cw);
       }
-      // settle undecided elements (rare) with the exact sequence, one per lane per round
+      // settle undecided elements (rare) with the exact sequences, one per lane per round
       while (__any_sync(0xffffffffu, pend != 0u)) {
         int b = 0;
-        bool binned = false;
+        bool binned = false, pass = false;
         if (pend) {
           const int k = __ffs(pend) - 1;
           pend &= pend - 1;
           const int u = k / V::N, v = k % V::N;
-          T pk = pe[0][0], xk = xe[0][0];
-#pragma unroll
-          for (int uu = 0; uu < K1_UNROLL; ++uu)
-#pragma unroll
-            for (int vv = 0; vv < V::N; ++vv)
-              if (uu == u && vv == v) { pk = pe[uu][vv]; xk = xe[uu][vv]; }
-          binned = Classifier<T>::exact(pk, xk, c, b) == 1;
-          codes[(base + u * 32 + lane) * V::N + v] = bin_code(h, binned, b);
+          const int64_t j = (base + u * 32 + lane) * V::N + v;   // reloaded: keeps pe, xe short-lived
+          binned = Classifier<T>::exact(prev[j], cur[j], c, h.cbase, b, pass) == 1;
+          codes[j] = (unsigned short)bin_code(h, binned, b, pass);
           if (binned) { lmin = min(lmin, b); lmax = max(lmax, b); }
         }
         hist_add(h, binned, b);
@@ -222,10 +252,12 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_hist(const T* __restrict__ p
     if (t0 < n && gwarp == 0) {
       const int64_t j = t0 + lane;
       int b = 0;
-      bool binned = false;
-      if (j < n) binned = Classifier<T>::exact(ld_stream(prev + j), ld_stream(cur + j), c, b) == 1;
+      bool binned = false, pass = false;
+      if (j < n)
+        binned = Classifier<T>::exact(ld_stream(prev + j), ld_stream(cur + j), c, h.cbase, b,
+                                      pass) == 1;
       if (binned) { lmin = min(lmin, b); lmax = max(lmax, b); }
-      if (j < n) codes[j] = bin_code(h, binned, b);
+      if (j < n) codes[j] = (unsigned short)bin_code(h, binned, b, pass);
       hist_add(h, binned, b);
     }
   } else {
@@ -243,9 +275,10 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_hist(const T* __restrict__ p
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         int b = 0;
-        const bool binned = ok[u] && Classifier<T>::exact(pe[u], xe[u], c, b) == 1;
+        bool pass = false;
+        const bool binned = ok[u] && Classifier<T>::exact(pe[u], xe[u], c, h.cbase, b, pass) == 1;
         if (binned) { lmin = min(lmin, b); lmax = max(lmax, b); }
-        if (ok[u]) codes[base + u * 32 + lane] = bin_code(h, binned, b);
+        if (ok[u]) codes[base + u * 32 + lane] = (unsigned short)bin_code(h, binned, b, pass);
         hist_add(h, binned, b);
       }
     }

@@ -216,8 +216,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_topk(TopkArgs A, Consts<T> c
   for (int r = tid; r < (1 << g.B); r += K2_THREADS) {
     T cr = (T)0, m = (T)1;
     if (r < n_sel) {
-      const T bf = (T)A.selb[r];
-      cr = t_add(a, t_mul(t_add(bf, (T)0.5), c.w));
+      cr = bin_centre<T>(A.selb[r], a, c.w);
       m = t_add((T)1, cr);
     }
     centres[r] = cr;
@@ -262,6 +261,8 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_topk(TopkArgs A, Consts<T> c
     ctrl->any = any && R > 0;
     ctrl->sel_bmin = bmin;
     ctrl->sel_bmax = bmax;
+    ctrl->sel_lo = n_sel > 0 ? A.selb[0] : 1;            // ranks follow ascending bin order
+    ctrl->sel_hi = n_sel > 0 ? A.selb[n_sel - 1] : 0;
     ctrl->n_sel = n_sel;
     ctrl->a = (double)a;
   }

@@ -237,3 +237,63 @@ def test_repeatable_and_workspace_reuse():
     gpu_compress(q.to(DEV), y.to(DEV), 1e-4, 10, anchor=N.ANCHOR_MIN)
     _, _, second = gpu_compress(pd, xd, 1e-3, 8)
     assert first == second
+
+
+def _fraction_pair(n, frac, T, seed):
+    """A pair whose incompressible fraction is close to `frac` at E = 1e-4, B = 4: the bulk
+    moves by a ratio inside two bins, the chosen fraction by ratios spread over thousands."""
+    rng = np.random.default_rng(seed)
+    p = rng.lognormal(0.0, 1.0, n)
+    r = np.where(rng.random(n) < 0.5, 1e-5, 3.1e-4)
+    far = rng.random(n) < frac
+    r[far] = rng.uniform(0.3, 0.9, int(far.sum()))
+    return p.astype(T), (p * (1.0 + r)).astype(T)
+
+
+@pytest.mark.parametrize("T,frac,n", [(np.float64, 0.7, 5_000_017), (np.float64, 0.8, 5_000_017),
+                                      (np.float64, 1.0, (1 << 24) + 12_345),
+                                      (np.float32, 0.4, 5_000_017), (np.float32, 0.6, 5_000_017),
+                                      (np.float32, 0.95, (1 << 24) + 12_345)])
+def test_high_incompressible_fractions(T, frac, n):
+    """Incompressible fractions on both sides of the point where the incompressible table can
+    reach the scratch area in the blob tail (75% for float64, 50% for float32), at sizes of
+    thousands of sub-blocks (several waves of the copy kernel)."""
+    p, x = _fraction_pair(n, frac, T, seed=int(frac * 100) + (T == np.float32))
+    h, _ = check_pair(p, x, 1e-4, 4, ranges=[(n // 3, 70_000), (n - 5000, 5000)])
+    L = np.dtype(T).itemsize
+    assert abs(h["n_inc"] / n - frac) < 0.05
+    assert (h["n_inc"] * L > n * (L - 2)) == (frac > (L - 2) / L)
+
+
+_BOUNDARY_BINS = (0, 1, -1, 5, -7, 100, -250, 1000, 5000, -9000, 16000, 16382, 16383, 16384,
+                  -16383, -16384, 20000, -30000)
+
+
+def _check_boundary_pair(T, E, per_bin=3000, seed=17):
+    """Points a few ulps either side of the error bound |p m - x| = E |x| (§III.C) of their
+    own bin, for bins near the zero change and far from it (beyond +-16383 bins as well)."""
+    rng = np.random.default_rng(seed)
+    Et = T(E)
+    w = T(Et + Et)
+    a = T(-Et)
+    ps, xs = [], []
+    for b in _BOUNDARY_BINS:
+        m = T(T(1) + T(a + T(T(b) + T(0.5)) * w))
+        p = rng.lognormal(size=per_bin).astype(T)
+        R = (p * m).astype(T)
+        sign = rng.choice([-1.0, 1.0], per_bin)
+        x = (R.astype(np.float64) / (1.0 + sign * float(Et))).astype(T)
+        x = (x + rng.integers(-3, 4, per_bin).astype(T) * np.spacing(x)).astype(T)
+        ps.append(p)
+        xs.append(x)
+    order = rng.permutation(per_bin * len(_BOUNDARY_BINS))
+    return np.concatenate(ps)[order], np.concatenate(xs)[order]
+
+
+@pytest.mark.parametrize("T", [np.float32, np.float64])
+@pytest.mark.parametrize("E", [1e-3, 3.3e-5])
+@pytest.mark.parametrize("anchor", [N.ANCHOR_ZERO, N.ANCHOR_MIN])
+def test_check_boundary_near_and_far_bins(T, E, anchor):
+    p, x = _check_boundary_pair(T, E)
+    h, _ = check_pair(p, x, E, 8, anchor=anchor)
+    assert 0 < h["n_inc"] < h["n"]
