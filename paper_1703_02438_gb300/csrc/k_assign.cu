@@ -95,12 +95,12 @@ struct Bits<double> {
 };
 
 
-constexpr int K3_WARPS = 16;                    // warps per CTA; each warp owns whole tiles
+constexpr int K3_WARPS = 32;                    // warps per CTA; each warp owns whole tiles
 constexpr int K3_THREADS = K3_WARPS * 32;
 constexpr int K3_SEG = 128;                     // elements per warp step: 4 consecutive per lane
 constexpr int K3_UNROLL = 4;                    // steps whose code loads are in flight together
 constexpr int STEPS = SUB / 32;                 // 32-element ballot words per tile
-constexpr int K3_SMEM = (CODE_BINS + 1) * 2;    // code-bin rank table (bytes)
+constexpr int K3_SMEM = 65536 * 2;              // index of every 16-bit code (bytes)
 
 // K3a — indexing and packing, from K1's codes alone. One warp processes one 4096-element tile at
 // a time (tile gw, gw + W, ... for global warp gw of W), in 128-element steps where lane l holds
@@ -217,9 +217,13 @@ __device__ __forceinline__ void anchor_consts(Consts<T>& c, const Geometry& g, c
 }
 
 template <typename T, int B>
-__global__ void __launch_bounds__(K3_THREADS, 2) k3_assign(AssignArgs<T> A) {
+__global__ void __launch_bounds__(K3_THREADS, 1) k3_assign(AssignArgs<T> A) {
   constexpr unsigned M = (1u << B) - 1u;
-  extern __shared__ unsigned short s_tab[];     // [CODE_BINS + 1]: rank of code bin i, or M
+  // CODE_FAR's entry: a value above M when B < 16 (max() over a tile finds far points, min()
+  // turns them into markers); M when B = 16, where far points are found by comparing codes
+  constexpr bool kSentinel = B < 16;
+  constexpr unsigned FARV = kSentinel ? 0xFFFFu : M;
+  extern __shared__ __align__(16) unsigned short s_tab[];   // [65536]: index of each code
 
   const Geometry& g = A.g;
   const Ctrl* ctrl = A.ctrl;
@@ -229,14 +233,15 @@ __global__ void __launch_bounds__(K3_THREADS, 2) k3_assign(AssignArgs<T> A) {
   const int cbase = ctrl->code_base;
   const int slo = any ? ctrl->sel_lo : 1, shi = any ? ctrl->sel_hi : 0;
 
-  // rank of every bin of the code window (entry CODE_BINS, reached by CODE_NONE and CODE_FAR,
-  // is M); bins outside the selected range are M without a lookup
-  for (int i = tid; i <= CODE_BINS; i += K3_THREADS) {
-    const int b = cbase + i;
-    s_tab[i] = (i < CODE_BINS && b >= slo && b <= shi) ? A.rank_of[b - A.c.hbase]
-                                                        : (unsigned short)M;
-  }
-  __syncthreads();   // the only block-wide barrier: the table is read-only from here on
+  // every code is a marker (M) except the pass codes of selected bins, which take the bin's rank
+  const uint4 fill = make_uint4(M | (M << 16), M | (M << 16), M | (M << 16), M | (M << 16));
+  for (int i = tid; i < 65536 / 8; i += K3_THREADS) reinterpret_cast<uint4*>(s_tab)[i] = fill;
+  __syncthreads();
+  const int blo = max(slo, cbase), bhi = min(shi, cbase + CODE_BINS - 1);
+  for (int b = blo + tid; b <= bhi; b += K3_THREADS)
+    s_tab[((b - cbase) << 1) | 1] = A.rank_of[b - A.c.hbase];
+  if (tid == 0) s_tab[CODE_FAR] = (unsigned short)FARV;
+  __syncthreads();   // the only block-wide barriers: the table is read-only from here on
 
   const long long W = (long long)gridDim.x * K3_WARPS;
   for (long long gt = (long long)blockIdx.x * K3_WARPS + (tid >> 5); gt < g.nsub; gt += W) {
@@ -245,7 +250,7 @@ __global__ void __launch_bounds__(K3_THREADS, 2) k3_assign(AssignArgs<T> A) {
     const unsigned short* ct = A.codes + tr.j0;
     const bool al = (tr.j0 & 3) == 0;           // codes of the tile 8-byte aligned
     int count = 0;
-    unsigned far = 0;                            // CODE_FAR seen (indexed as M for now)
+    unsigned far = 0;                            // > M (B < 16) or non-zero: CODE_FAR seen
     for (int s0 = 0; s0 < cnt; s0 += K3_SEG * K3_UNROLL) {
       uint2 cd[K3_UNROLL];   // four 16-bit codes per lane and step
 #pragma unroll
@@ -268,15 +273,20 @@ __global__ void __launch_bounds__(K3_THREADS, 2) k3_assign(AssignArgs<T> A) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const unsigned cv = ((k < 2 ? cd[u].x : cd[u].y) >> (16 * (k & 1))) & 0xFFFFu;
-          const unsigned r = s_tab[cv >> 1];
-          idx[k] = (cv & 1u) ? r : M;            // pass bit clear (or CODE_NONE): marker
-          far |= cv == CODE_FAR ? 1u : 0u;
+          const unsigned r = s_tab[cv];
+          if constexpr (kSentinel) {
+            far = max(far, r);
+            idx[k] = min(r, M);
+          } else {
+            far |= cv == CODE_FAR ? 1u : 0u;
+            idx[k] = r;
+          }
         }
         step_out<B>(idx, sb0, cnt, lane, tr.halves, tr.tw, tr.twords, count);
       }
     }
     count = __reduce_add_sync(0xffffffffu, count);
-    const bool fix = any && __any_sync(0xffffffffu, far != 0u);
+    const bool fix = any && __any_sync(0xffffffffu, kSentinel ? far > M : far != 0u);
     if (lane == 0) A.tstatus[gt] = (unsigned long long)count | (fix ? K3_FAR_FLAG : 0ull);
   }
 }

@@ -74,16 +74,21 @@ __device__ __forceinline__ unsigned bin_code(const HistCtx& h, bool binned, int 
   return off < (unsigned)CODE_BINS ? (off << 1) | (pass ? 1u : 0u) : CODE_FAR;
 }
 
-// All 32 lanes call this together (valid may differ per lane).
-__device__ __forceinline__ void hist_add(const HistCtx& h, bool valid, int b) {
+// All 32 lanes call this together (valid may differ per lane). lt = lanes below this one. Bins
+// outside the shared window also update this thread's bin range (the range of the bins inside
+// it is read from the shared histogram at the end).
+__device__ __forceinline__ void hist_add(const HistCtx& h, bool valid, int b, unsigned lt,
+                                         int& lmin, int& lmax) {
   const unsigned key = valid ? (unsigned)b : 0x80000000u;   // INT_MIN is never a bin
   const unsigned peers = __match_any_sync(0xffffffffu, key);
-  if (valid && (int)lane_id() == __ffs(peers) - 1) {
+  if (valid && (peers & lt) == 0u) {                         // lowest lane of its group
     const unsigned cnt = __popc(peers);
     const int si = b - h.sbase;
     if ((unsigned)si < (unsigned)SH_BINS) {
       atomicAdd(&h.sh[si], cnt);
     } else {
+      lmin = min(lmin, b);
+      lmax = max(lmax, b);
       const int gi = b - h.hbase;
       if ((unsigned)gi < (unsigned)HWIN)
         atomicAdd(&h.hist[gi], (unsigned long long)cnt);
@@ -192,6 +197,7 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_hist(const T* __restrict__ p
 
   int lmin = 0x7FFFFFFF, lmax = (int)0x80000000;
   const int lane = (int)lane_id();
+  const unsigned lt = lanemask_lt();
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
 
@@ -224,10 +230,9 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_hist(const T* __restrict__ p
           bool pass = false;
           const int kind = ok[u] ? Classifier<T>::fast(pe[u][v], xe[u][v], c, h.cbase, b, pass) : 0;
           const bool binned = kind == 1;
-          if (binned) { lmin = min(lmin, b); lmax = max(lmax, b); }
           if (kind >= 2) pend |= 1u << (u * V::N + v);
           cw[v] = bin_code(h, binned, b, pass);
-          hist_add(h, binned, b);
+          hist_add(h, binned, b, lt, lmin, lmax);
         }
         if (ok[u]) reinterpret_cast<typename V::codes*>(codes)[vi] = V::pack(cw);
       }
@@ -242,9 +247,8 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_hist(const T* __restrict__ p
           const int64_t j = (base + u * 32 + lane) * V::N + v;   // reloaded: keeps pe, xe short-lived
           binned = Classifier<T>::exact(prev[j], cur[j], c, h.cbase, b, pass) == 1;
           codes[j] = (unsigned short)bin_code(h, binned, b, pass);
-          if (binned) { lmin = min(lmin, b); lmax = max(lmax, b); }
         }
-        hist_add(h, binned, b);
+        hist_add(h, binned, b, lt, lmin, lmax);
       }
     }
     // scalar tail (< V elements), one warp
@@ -256,9 +260,8 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_hist(const T* __restrict__ p
       if (j < n)
         binned = Classifier<T>::exact(ld_stream(prev + j), ld_stream(cur + j), c, h.cbase, b,
                                       pass) == 1;
-      if (binned) { lmin = min(lmin, b); lmax = max(lmax, b); }
       if (j < n) codes[j] = (unsigned short)bin_code(h, binned, b, pass);
-      hist_add(h, binned, b);
+      hist_add(h, binned, b, lt, lmin, lmax);
     }
   } else {
     constexpr int U = 8;
@@ -277,17 +280,30 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_hist(const T* __restrict__ p
         int b = 0;
         bool pass = false;
         const bool binned = ok[u] && Classifier<T>::exact(pe[u], xe[u], c, h.cbase, b, pass) == 1;
-        if (binned) { lmin = min(lmin, b); lmax = max(lmax, b); }
         if (ok[u]) codes[base + u * 32 + lane] = (unsigned short)bin_code(h, binned, b, pass);
-        hist_add(h, binned, b);
+        hist_add(h, binned, b, lt, lmin, lmax);
       }
     }
   }
 
-  // bin range of this CTA -> one atomic per CTA on each key
+  // merge the shared window into the global histogram; the bins it holds extend the range
   __shared__ int s_min, s_max;
   if (threadIdx.x == 0) { s_min = 0x7FFFFFFF; s_max = (int)0x80000000; }
-  __syncthreads();
+  __syncthreads();   // every shared-histogram update is done
+  for (int i = threadIdx.x; i < SH_BINS; i += blockDim.x) {
+    const unsigned v = sh[i];
+    if (v) {
+      const int b = h.sbase + i;
+      lmin = min(lmin, b);
+      lmax = max(lmax, b);
+      const int gi = b - h.hbase;
+      if ((unsigned)gi < (unsigned)HWIN)
+        atomicAdd(&hist[gi], (unsigned long long)v);
+      else
+        atomicOr(&ctrl->win_err, 1u);
+    }
+  }
+  // bin range of this CTA -> one atomic per CTA on each key
   lmin = __reduce_min_sync(0xffffffffu, lmin);
   lmax = __reduce_max_sync(0xffffffffu, lmax);
   if (lane == 0 && lmin <= lmax) { atomicMin(&s_min, lmin); atomicMax(&s_max, lmax); }
@@ -295,17 +311,6 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_hist(const T* __restrict__ p
   if (threadIdx.x == 0 && s_min <= s_max) {
     atomicMax(&ctrl->bmin_key, KEY_BIAS - (unsigned)s_min);
     atomicMax(&ctrl->bmax_key, (unsigned)s_max + KEY_BIAS);
-  }
-  // merge the shared window into the global histogram
-  for (int i = threadIdx.x; i < SH_BINS; i += blockDim.x) {
-    const unsigned v = sh[i];
-    if (v) {
-      const int gi = h.sbase + i - h.hbase;
-      if ((unsigned)gi < (unsigned)HWIN)
-        atomicAdd(&hist[gi], (unsigned long long)v);
-      else
-        atomicOr(&ctrl->win_err, 1u);
-    }
   }
 }
 
