@@ -26,6 +26,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -51,7 +53,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 24,
                     help="elements of the oracle's bounded sample")
-    ap.add_argument("--workload", default="flash", choices=["flash", "batched"],
+    ap.add_argument("--auto-b", action="store_true",
+                    help="choose B per pair from the histogram (Eqs. 5-6) instead of B = 8, 10")
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--workload", default="flash", choices=["flash", "batched", "served"],
                     help="flash: the headline 1024^3 series; batched: 256 mixed variables, "
                          "per-variable launches vs one graph-captured batch")
     ap.add_argument("--batch-count", type=int, default=256)
@@ -306,6 +312,119 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_served(args):
+    """The served form: 32 series (sizes log-uniform in [1 MB, 2 GB] of float32/float64 data,
+    50/50), Poisson arrivals at --serve-rate requests/s for --serve-seconds; 80% compressions of
+    the next timestep, 20% decompressions of the latest one (half whole, half a 1-10% range at
+    a random start). Reports latency percentiles from the server's own timestamps (completion -
+    submission, the request being submitted at its arrival time) and the aggregate input GB/s."""
+    import torch
+    from paper_1703_02438_gb300 import build as nbuild
+    from paper_1703_02438_gb300 import numarck as N
+    from paper_1703_02438_gb300 import synth
+    nbuild.build()
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(synth.seed_for(4))
+    n_series, steps = 32, 3
+    series = []
+    for s_ in range(n_series):
+        size = int(np.exp(rng.uniform(np.log(1 << 20), np.log(2 << 30))))
+        dtype = torch.float64 if rng.random() < 0.5 else torch.float32
+        L = 8 if dtype == torch.float64 else 4
+        n = max(1, size // L)
+        g = torch.Generator(device=dev)
+        g.manual_seed(synth.seed_for(4, s_))
+        x = torch.empty(n, dtype=torch.float64, device=dev).log_normal_(0.0, 1.0, generator=g)
+        ts = []
+        for t in range(steps):
+            if t:
+                r = torch.randn(n, generator=g, device=dev, dtype=torch.float64).mul_(1e-3)
+                x = x * (1.0 + r)
+            h = torch.empty(n, dtype=dtype, pin_memory=True)
+            h.copy_(x.to(dtype))
+            ts.append(h)
+        params = N.make_params(dtype, (6, 8, 10)[s_ % 3], (1e-3, 1e-4)[s_ % 2])
+        out_blob = torch.empty(N.compress_bound(n, params), dtype=torch.uint8, pin_memory=True)
+        out_dec = torch.empty(n, dtype=dtype, pin_memory=True)
+        series.append(dict(n=n, L=L, ts=ts, params=params, blob=out_blob, dec=out_dec))
+        del x
+    torch.cuda.synchronize()
+    arena = torch.empty(64 << 30, dtype=torch.uint8, device=dev)
+    srv = N.Server(arena, slots=8, max_series=n_series)
+    for s_, sr in enumerate(series):                  # reference timesteps (not timed)
+        srv.submit(N.REQ_COMPRESS, s_, sr["n"], sr["params"], host_in=sr["ts"][0],
+                   host_out=sr["blob"])
+    got = 0
+    while got < n_series:
+        got += len(srv.poll(wait_ms=100))
+    next_t = [1] * n_series
+    compressed = [False] * n_series          # a decompression needs a compressed timestep
+    arrivals = np.cumsum(rng.exponential(1.0 / args.serve_rate,
+                                         int(args.serve_rate * args.serve_seconds * 1.2) + 10))
+    arrivals = arrivals[arrivals < args.serve_seconds]
+    kinds = rng.random(arrivals.size)
+    picks = rng.integers(0, n_series, arrivals.size)
+    info, done = {}, []
+    t0 = time.perf_counter()
+    for a_t, k, s_ in zip(arrivals, kinds, picks):
+        while True:
+            now = time.perf_counter() - t0
+            if now >= a_t:
+                break
+            done += srv.poll(wait_ms=0)
+            time.sleep(min(0.0005, a_t - now))
+        sr = series[s_]
+        if k < 0.8 or not compressed[s_]:
+            compressed[s_] = True
+            t = next_t[s_]
+            next_t[s_] = t % (steps - 1) + 1
+            rid = srv.submit(N.REQ_COMPRESS, int(s_), sr["n"], sr["params"], host_in=sr["ts"][t],
+                             host_out=sr["blob"])
+            info[rid] = ("compress", sr["n"] * sr["L"])
+        else:
+            if k < 0.9:
+                start, count = 0, sr["n"]
+            else:
+                count = max(1, int(sr["n"] * rng.uniform(0.01, 0.10)))
+                start = int(rng.integers(0, sr["n"] - count + 1))
+            rid = srv.submit(N.REQ_DECOMPRESS, int(s_), sr["n"], sr["params"],
+                             host_out=sr["dec"][:count], start=start, count=count)
+            info[rid] = ("decompress", count * sr["L"])
+    while len(done) < len(info):
+        done += srv.poll(wait_ms=100)
+    st = srv.stats()
+    srv.close()
+    ok = [c for c in done if c["status"] == 0]
+    lat = {"compress": [], "decompress": []}
+    for c in ok:
+        lat[info[c["id"]][0]].append((c["t_end"] - c["t_submit"]) * 1e3)
+    span = max(c["t_end"] for c in done) - min(c["t_submit"] for c in done)
+    moved = sum(info[c["id"]][1] for c in ok)
+    offered = sum(v[1] for v in info.values()) / args.serve_seconds / 1e9
+    allv = lat["compress"] + lat["decompress"]
+    pct = lambda v, q: float(np.percentile(v, q)) if v else None
+    line = {"metric": "served compress/decompress requests: latency p50/p99 and aggregate input GB/s",
+            "value": moved / span / 1e9, "unit": "GB/s", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": f"{n_series} series, sizes log-uniform [1 MB, 2 GB], float32/"
+                                   f"float64 50/50, Poisson {args.serve_rate:g} req/s for "
+                                   f"{args.serve_seconds:g} s, 80% compress / 20% decompress "
+                                   "(half whole, half 1-10% range)",
+                       "slots": 8, "arena_gb": 64},
+            "requests": len(info), "completed_ok": len(ok),
+            "failed": len(done) - len(ok),
+            "failed_status": {str(k): v for k, v in
+                              sorted(__import__("collections").Counter(
+                                  c["status"] for c in done if c["status"]).items())},
+            "offered_gbs": offered,
+            "p50_ms": pct(allv, 50), "p99_ms": pct(allv, 99),
+            "compress_p50_ms": pct(lat["compress"], 50), "compress_p99_ms": pct(lat["compress"], 99),
+            "decompress_p50_ms": pct(lat["decompress"], 50),
+            "decompress_p99_ms": pct(lat["decompress"], 99),
+            "server": {k: st[k] for k in ("deferred_memory", "arena_peak", "max_inflight")}}
+    print(json.dumps(line), flush=True)
+
+
 def run_e2e(args, xs, n, bound, dist, dev, ws):
     """End-to-end metric through the public API: host timesteps in, blobs and reconstructions
     out, with host<->device copies overlapped with the kernels (see the comment in main)."""
@@ -432,6 +551,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "served":
+        return run_served(args)
     if args.workload == "batched":
         return run_batched(args)
     rank, world = _rank_world()
@@ -454,7 +575,8 @@ def main():
     n = side ** 3
     xs = synth.flash_series(side=side, steps=4, device=dev, seed=synth.seed_for(1, rank))
     torch.cuda.synchronize()
-    params = {(E, B): N.make_params(torch.float64, B, E) for E, B in COMBOS}
+    combos = [(E, 0 if args.auto_b else B) for E, B in COMBOS]
+    params = {(E, B): N.make_params(torch.float64, B, E) for E, B in combos}
     bound = max(N.compress_bound(n, p) for p in params.values())
     blob = torch.empty(bound, dtype=torch.uint8, device=dev)
     recon = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(2)]
@@ -474,7 +596,7 @@ def main():
         return evs
 
     def step(trace: bool):
-        for E, B in COMBOS:
+        for E, B in combos:
             prev = xs[0]
             for t in range(1, 4):
                 if trace:
@@ -580,8 +702,9 @@ def main():
             "compress_path_hbm_frac": comp_alg / (t_comp / 1e3) / 1e9 / peak,
             "compress_one_pass_frac": one_pass / (t_comp / 1e3) / 1e9 / peak,
             "decompress_gbs": n * 8 / (avg["k4_decode"] / 1e3) / 1e9,
-            "alpha_last": alpha, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
-            "gpu_launches": args.steps * n_pairs * 7,
+            "alpha_last": alpha, "B_last": Bl, "auto_b": bool(args.auto_b),
+            "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": args.steps * n_pairs * (8 if args.auto_b else 7),
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -80,7 +80,8 @@ typedef struct CUstream_st* numarck_stream_t;
 /* Compression parameters (user-controllable parameters of §IV.B.2 and §IV.C). */
 typedef struct numarck_params {
   int32_t dtype;        /* NUMARCK_F32 or NUMARCK_F64                                     */
-  int32_t B;            /* index bits, 1..16; k = 2^B - 1 bins, marker M = 2^B - 1         */
+  int32_t B;            /* index bits, 1..16 (k = 2^B - 1 bins, marker M = 2^B - 1), or 0:  *
+                         * chosen from the histogram by Eqs. 5-6 (§IV.B.2; see below)     */
   double  E;            /* error bound, 2^-60 <= E < 1; bin width is 2E (§IV.B.1)          */
   int32_t anchor;       /* NUMARCK_ANCHOR_ZERO or NUMARCK_ANCHOR_MIN                      */
   int32_t reserved;     /* must be 0                                                       */
@@ -171,12 +172,13 @@ typedef struct numarck_header {
 
 /* ---- sizing (host only; never touch the device) ---- */
 
-/* Bytes a blob can need for n elements: every section sized for the worst case n_inc = n.
- * Returns 0 if n or *p is invalid. */
+/* Bytes a blob can need for n elements: every section sized for the worst case n_inc = n
+ * (for B = 0: the largest over B = 1..16, i.e. B = 16). Returns 0 if n or *p is invalid. */
 size_t numarck_compress_bound(int64_t n, const numarck_params* p);
 
 /* Bytes of device workspace numarck_compress needs for n elements (histogram window of
- * 2^22 + 16 bins, rank table, per-sub-block scan state). Returns 0 if invalid. */
+ * 2^22 + 16 bins, rank table, per-sub-block scan state; for B = 0 sized for B = 16).
+ * Returns 0 if invalid. */
 size_t numarck_workspace_bytes(int64_t n, const numarck_params* p);
 
 /* Zero-fills a workspace (asynchronous on stream). A workspace must be zero-filled once
@@ -199,7 +201,15 @@ int numarck_workspace_init(void* ws, size_t ws_bytes, numarck_stream_t stream);
  *             aligned, zero-filled before first use (numarck_workspace_init). Two calls
  *             that overlap in time must not share a workspace.
  * stream    : the stream the work is queued on.
- * Returns NUMARCK_OK once the work is queued (host-side errors as listed above). */
+ * Returns NUMARCK_OK once the work is queued (host-side errors as listed above).
+ *
+ * Automatic index length (p->B = 0, §IV.B.2): after the histogram pass the library evaluates
+ * file_size(B) = 2^B * L + n * B / 8 + n * alpha(B) * L (Eqs. 5, 6) for B = 1..16, where
+ * alpha(B) counts as compressible every point of the 2^B - 1 most populated bins, and keeps
+ * the smallest (ties: smaller B). The rest of the layout depends on B, so the call reads the
+ * choice back (it synchronises `stream` once) and then queues the remaining kernels; the
+ * chosen B is in the blob header. It returns NUMARCK_ERR_INVALID_ARG while `stream` is being
+ * captured into a graph, and the batch entry points reject B = 0. */
 int numarck_compress(const void* prev, const void* cur, int64_t n, const numarck_params* p,
                      void* blob, size_t blob_cap, void* ws, size_t ws_bytes,
                      numarck_stream_t stream);
@@ -335,6 +345,93 @@ const char* numarck_status_string(int code);
 
 /* Library version string, e.g. "numarck-gb300 1 sm_103a". */
 const char* numarck_version(void);
+
+/* ---- served form: a request loop over resident time series (§I in-situ use, §IV.D) ----
+ *
+ * A server takes one caller-owned device buffer (the arena) and serves compress and
+ * decompress requests for up to max_series time series from any number of client threads.
+ * For each series it keeps in the arena the last reconstruction (the prev of the series' next
+ * compression), the reconstruction the latest blob was compressed against, and the latest blob
+ * (capacity for any B). The first compress request of a series only stores its timestep as the
+ * reference (the caller keeps that timestep itself; completion.reference = 1); every later one
+ * compresses the new timestep against the series' last reconstruction (Eq. 1 against R_{i-1}),
+ * decodes the blob into the new reconstruction (Eq. 4) and copies the blob's used bytes to the
+ * caller. A decompress request decodes all or part ([start, start + count)) of the series'
+ * latest timestep from its latest blob into pinned host memory.
+ *
+ * Scheduling: the requests of one series run one at a time, in submission order. Across
+ * series, the oldest request that can run starts as soon as one of `slots` CUDA streams is free
+ * and its transient device buffers (a compression: the timestep and a workspace; a
+ * decompression: its output; a series' first compression: the series' resident buffers) fit
+ * in the arena's free space (first-fit); a younger request passes an older one that does not
+ * fit only if the older one still fits afterwards. A request that cannot fit even with nothing
+ * running completes with NUMARCK_ERR_CAPACITY. Results do not depend on what else runs: every
+ * request has its own workspace and stream, and the kernels are deterministic.
+ *
+ * All host buffers (host_in, host_out) must be pinned (cudaHostAlloc / registered) and stay
+ * valid until the request's completion is polled. Timestamps are seconds on the server's
+ * steady clock. With dry_run = 1 no CUDA call is made and arena may be NULL: each request stage
+ * takes dry_run_us microseconds (for tests of the scheduling on hosts without a GPU). */
+typedef struct numarck_server numarck_server;
+
+typedef struct numarck_server_config {
+  void*   arena;          /* device buffer, 256-byte aligned, owned by the caller             */
+  size_t  arena_bytes;
+  int32_t slots;          /* requests in flight at once (one CUDA stream each), 1..64        */
+  int32_t max_series;     /* series ids 0..max_series-1, 1..2^20                             */
+  int32_t dry_run;        /* 0, or 1: no CUDA calls (see above)                              */
+  int32_t dry_run_us;     /* dry run: duration of each request stage in microseconds         */
+} numarck_server_config;
+
+#define NUMARCK_REQ_COMPRESS   0
+#define NUMARCK_REQ_DECOMPRESS 1
+
+typedef struct numarck_request {
+  int32_t kind;           /* NUMARCK_REQ_COMPRESS or NUMARCK_REQ_DECOMPRESS                   */
+  int32_t series;         /* 0..max_series-1                                                  */
+  numarck_params params;  /* compress: dtype, B (1..16), E, anchor, block size; decompress:    *
+                           * dtype (must be the series')                                      */
+  int64_t n;              /* elements of the series (fixed by its first timestep)            */
+  const void* host_in;    /* compress: the new timestep, n elements of T, pinned             */
+  void*   host_out;       /* compress: the blob; decompress: count elements of T; pinned     */
+  size_t  host_out_cap;   /* bytes at host_out                                               */
+  int64_t start, count;   /* decompress: elements [start, start + count) of the timestep     */
+} numarck_request;
+
+typedef struct numarck_completion {
+  uint64_t id;            /* as returned by numarck_server_submit                             */
+  int32_t status;         /* NUMARCK_OK or an error code (CAPACITY: host_out too small, or the *
+                           * request can never fit in the arena; INVALID_ARG: n or dtype not   *
+                           * the series', or a decompression before any compression)          */
+  int32_t kind, series;
+  int32_t reference;      /* 1: the series' first timestep, stored as its reference           */
+  int32_t pad;
+  uint64_t out_bytes;     /* bytes written to host_out                                        */
+  double  t_submit, t_start, t_end;
+} numarck_completion;
+
+typedef struct numarck_server_stats {
+  uint64_t submitted, started, completed;
+  uint64_t deferred_memory;   /* admission attempts deferred for lack of arena space         */
+  uint64_t arena_bytes, arena_used, arena_peak;
+  int32_t  max_inflight, pad;
+  double   now;
+} numarck_server_stats;
+
+/* Creates a server (starts its worker thread on the current device). Returns NULL and sets
+ * *status (if non-NULL) on invalid configuration or CUDA errors. */
+numarck_server* numarck_server_create(const numarck_server_config* cfg, int* status);
+/* Queues a request (thread-safe, never blocks on the GPU); *id receives its id. Returns
+ * NUMARCK_ERR_INVALID_ARG for malformed requests (series out of range, bad params, B = 0). */
+int numarck_server_submit(numarck_server* s, const numarck_request* r, uint64_t* id);
+/* Moves up to max completions (oldest first) to out, waiting up to wait_ms for the first one;
+ * *got receives their number. */
+int numarck_server_poll(numarck_server* s, numarck_completion* out, int max, int* got,
+                        int wait_ms);
+int numarck_server_get_stats(numarck_server* s, numarck_server_stats* out);
+/* Runs every submitted request to completion, then frees the server's streams and events
+ * (the arena stays the caller's). */
+int numarck_server_destroy(numarck_server* s);
 
 #ifdef __cplusplus
 }  /* extern "C" */

@@ -36,6 +36,9 @@ listed in DESIGN.md):
       first; block byte images are padded with zero bytes to a multiple of 16.
   R9  offset tables are int64 with nblocks + 1 entries; a sub-block table (one int64 per
       4096 elements) is added for decoders.
+  R10 automatic index length (§IV.B.2): B ranges over 1..16; alpha(B) of Eq. 5 counts as
+      compressible every point of the top 2^B - 1 bins (the histogram's estimate, before
+      the error check); the smallest file_size(B) of Eq. 6 wins, ties to the smaller B.
 """
 from __future__ import annotations
 
@@ -138,6 +141,26 @@ def top_k(bins: np.ndarray, counts: np.ndarray, k: int) -> np.ndarray:
     returned in ascending bin order; position in the result = the bin's index r."""
     order = np.lexsort((bins, -counts))      # last key is primary: count descending
     return np.sort(bins[order[:k]])
+
+
+def file_size_bits(counts: np.ndarray, n: int, L: int, B_max: int = 16) -> list:
+    """8 * file_size(B) of Eq. 6 for B = 1..B_max (§IV.B.2): the compressible points are those
+    in the top k = 2^B - 1 bins of the histogram (reading R10), alpha(B) of Eq. 5 is
+    (n - compressible) / n, file_size(B) = 2^B * L + n * B / 8 + n * alpha(B) * L. Exact
+    integers (bits), so that sizes compare without rounding."""
+    desc = np.sort(np.asarray(counts, dtype=np.int64))[::-1]
+    prefix = np.concatenate([[0], np.cumsum(desc, dtype=np.int64)])
+    out = []
+    for B in range(1, B_max + 1):
+        compressible = int(prefix[min((1 << B) - 1, desc.size)])
+        out.append(8 * (1 << B) * L + n * B + 8 * L * (n - compressible))
+    return out
+
+
+def choose_B(counts: np.ndarray, n: int, L: int, B_max: int = 16) -> int:
+    """The B of smallest file_size(B) (§IV.B.2); ties go to the smaller B."""
+    bits = file_size_bits(counts, n, L, B_max)
+    return 1 + int(np.argmin(bits))          # argmin returns the first (smallest B) minimum
 
 
 def centres_of(selected: np.ndarray, a, w, T) -> np.ndarray:
@@ -266,18 +289,20 @@ def compress(prev: np.ndarray, cur: np.ndarray, E: float, B: int, anchor: int = 
     cur = np.ascontiguousarray(cur)
     assert prev.dtype == cur.dtype and prev.dtype in (np.float32, np.float64)
     assert prev.ndim == 1 and prev.shape == cur.shape
-    assert 1 <= B <= 16
+    assert 0 <= B <= 16                                              # 0: choose B (§IV.B.2)
     T = prev.dtype.type
     L = prev.dtype.itemsize
     n = prev.shape[0]
-    k = (1 << B) - 1
-    M = (1 << B) - 1
 
     E_T, w, inv_w, cap = grid_constants(T, E)
     ratio, binnable = change_ratio(prev, cur, cap)                   # Eq. 1
     a = grid_anchor(ratio, binnable, E_T, anchor)                    # R2
     b = bin_ids(ratio, binnable, a, inv_w)                           # R3
     bins, counts = histogram(b, binnable)                            # §IV.B.1
+    if B == 0:
+        B = choose_B(counts, n, L)                                   # §IV.B.2, Eqs. 5-6
+    k = (1 << B) - 1
+    M = (1 << B) - 1
     selected = top_k(bins, counts, k)                                # §IV.B.1
     c_sel = centres_of(selected, a, w, T)                            # R6
     idx = assign_indices(prev, cur, binnable, b, selected, c_sel, E_T, M)   # §III.C
@@ -319,8 +344,10 @@ def compress(prev: np.ndarray, cur: np.ndarray, E: float, B: int, anchor: int = 
 
 
 def compress_bound(n: int, T, B: int, block_bytes: int = DEFAULT_BLOCK_BYTES) -> int:
-    """Largest blob for n elements: all points incompressible."""
-    return layout(n, T, B, block_bytes)["off_exact"] + n * np.dtype(T).itemsize
+    """Largest blob for n elements: all points incompressible (B = 0, chosen at run time: the
+    largest over B = 1..16)."""
+    Bs = [B] if B else range(1, 17)
+    return max(layout(n, T, b, block_bytes)["off_exact"] for b in Bs) + n * np.dtype(T).itemsize
 
 
 # ---------------------------------------------------------------------------------------

@@ -90,6 +90,7 @@ int slices(const numarck_batch_item* items, int count, int lanes, std::vector<in
   *lane_of = assign_lanes(n.data(), dt.data(), count, lanes);
   std::vector<size_t> need(lanes, 0);
   for (int i = 0; i < count; ++i) {
+    if (items[i].params.B == 0) return NUMARCK_ERR_INVALID_ARG;   // automatic B synchronises
     const size_t w = numarck_workspace_bytes(items[i].n, &items[i].params);
     if (w == 0) return NUMARCK_ERR_INVALID_ARG;
     need[(*lane_of)[i]] = std::max(need[(*lane_of)[i]], w);

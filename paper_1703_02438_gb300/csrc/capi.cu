@@ -3,6 +3,7 @@
 // Host side only: argument validation, blob geometry (§IV.C block layout, §IV.D arrays),
 // workspace layout, and the launch sequence K0 (ANCHOR_MIN) -> K1 -> K2 -> K3a -> K3b -> K3c for
 // compression and K4 for (partial) decompression. Nothing here allocates device memory.
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstring>
@@ -30,7 +31,7 @@ float f_up(double v) {
 int check_params(const numarck_params* p) {
   if (!p) return NUMARCK_ERR_INVALID_ARG;
   if (p->dtype != NUMARCK_F32 && p->dtype != NUMARCK_F64) return NUMARCK_ERR_INVALID_ARG;
-  if (p->B < 1 || p->B > NUMARCK_MAX_B) return NUMARCK_ERR_INVALID_ARG;
+  if (p->B < 0 || p->B > NUMARCK_MAX_B) return NUMARCK_ERR_INVALID_ARG;   // 0: automatic
   if (!std::isfinite(p->E) || !(p->E >= 0x1p-60) || !(p->E < 1.0)) return NUMARCK_ERR_INVALID_ARG;
   if (p->anchor != NUMARCK_ANCHOR_ZERO && p->anchor != NUMARCK_ANCHOR_MIN)
     return NUMARCK_ERR_INVALID_ARG;
@@ -38,6 +39,21 @@ int check_params(const numarck_params* p) {
   if (p->block_bytes != 0 && (p->block_bytes < 2 || p->block_bytes > ((int64_t)1 << 30)))
     return NUMARCK_ERR_INVALID_ARG;
   return NUMARCK_OK;
+}
+
+// Geometry a call needs room for. For B = 0 (chosen after the histogram) it must cover every
+// B = 1..16: off_exact is the largest over B (so the blob bound and K1's code area fit any
+// layout) and nsub the largest over B (index blocks of any B end in a partial tile, so a
+// smaller B can have more sub-blocks); the other fields are those of B = 16.
+Geometry room_geometry(int64_t n, const numarck_params* p, int64_t bb) {
+  if (p->B) return make_geometry(n, p->dtype, p->B, bb, p->anchor);
+  Geometry g = make_geometry(n, p->dtype, NUMARCK_MAX_B, bb, p->anchor);
+  for (int B = 1; B < NUMARCK_MAX_B; ++B) {
+    const Geometry h = make_geometry(n, p->dtype, B, bb, p->anchor);
+    g.off_exact = std::max(g.off_exact, h.off_exact);
+    g.nsub = std::max(g.nsub, h.nsub);
+  }
+  return g;
 }
 
 int64_t effective_block_bytes(const numarck_params* p) {
@@ -158,14 +174,13 @@ extern "C" {
 
 size_t numarck_compress_bound(int64_t n, const numarck_params* p) {
   if (check_params(p) || n < 0 || n > MAX_N) return 0;
-  const Geometry g = make_geometry(n, p->dtype, p->B, effective_block_bytes(p), p->anchor);
+  const Geometry g = room_geometry(n, p, effective_block_bytes(p));
   return (size_t)(g.off_exact + n * (p->dtype == NUMARCK_F64 ? 8 : 4));
 }
 
 size_t numarck_workspace_bytes(int64_t n, const numarck_params* p) {
   if (check_params(p) || n < 0 || n > MAX_N) return 0;
-  const Geometry g = make_geometry(n, p->dtype, p->B, effective_block_bytes(p), p->anchor);
-  return make_ws(g).total;
+  return make_ws(room_geometry(n, p, effective_block_bytes(p))).total;
 }
 
 int numarck_workspace_init(void* ws, size_t ws_bytes, numarck_stream_t stream) {
@@ -190,7 +205,9 @@ int plan_compress(const void* prev, const void* cur, int64_t n, const numarck_pa
   if (n > 0 && (!prev || !cur || !aligned(prev, L) || !aligned(cur, L)))
     return NUMARCK_ERR_INVALID_ARG;
   const int64_t bb = effective_block_bytes(p);
-  const Geometry g = make_geometry(n, p->dtype, p->B, bb, p->anchor);
+  // for B = 0 only K0, K1 and the choice of B run on this geometry (K1 uses n, nsub and the
+  // code offset); the rest is planned again with the chosen B
+  const Geometry g = room_geometry(n, p, bb);
   const WsLayout wl = make_ws(g);
   if (blob_cap < (size_t)(g.off_exact + n * (int64_t)L)) return NUMARCK_ERR_CAPACITY;
   if (ws_bytes < wl.total) return NUMARCK_ERR_CAPACITY;
@@ -204,6 +221,8 @@ int plan_compress(const void* prev, const void* cur, int64_t n, const numarck_pa
   P.wl = wl;
   P.g = g;
   P.aligned16 = aligned(prev, 16) && aligned(cur, 16);
+  P.code_off = code_offset(g);
+  P.auto_b = p->B == 0;
   if (p->dtype == NUMARCK_F64)
     P.cd = make_consts<double>(p->E, p->anchor);
   else
@@ -214,7 +233,7 @@ int plan_compress(const void* prev, const void* cur, int64_t n, const numarck_pa
   h.magic = NUMARCK_MAGIC;
   h.version = NUMARCK_VERSION;
   h.dtype = p->dtype;
-  h.B = p->B;
+  h.B = p->B ? p->B : NUMARCK_MAX_B;
   h.E = p->E;
   h.anchor = p->anchor;
   h.status = 0;
@@ -236,12 +255,36 @@ int plan_compress(const void* prev, const void* cur, int64_t n, const numarck_pa
 }
 
 // Queues the kernels of a planned compression on stream s (P.sms must be set).
-int launch_compress(const CompressPlan& P, cudaStream_t s) {
+int launch_compress(const CompressPlan& P0, cudaStream_t s) {
   trace(0, 6, s);
-  if (P.g.anchor == NUMARCK_ANCHOR_MIN && launch_anchor_min(P, s) != cudaSuccess)
+  if (P0.g.anchor == NUMARCK_ANCHOR_MIN && launch_anchor_min(P0, s) != cudaSuccess)
     return NUMARCK_ERR_CUDA;
-  if (launch_hist(P, s) != cudaSuccess) return NUMARCK_ERR_CUDA;
+  if (launch_hist(P0, s) != cudaSuccess) return NUMARCK_ERR_CUDA;
   trace(1, 6, s);
+  CompressPlan P = P0;
+  if (P0.auto_b) {
+    // B from the histogram (§IV.B.2): the geometry of everything after K1 depends on it, so
+    // the host reads it back (one synchronisation) and plans the rest with it; K1's codes stay
+    // where the B = 16 layout put them (inside every layout's incompressible capacity)
+    if (launch_auto_b(P0, s) != cudaSuccess) return NUMARCK_ERR_CUDA;
+    int B = 0;
+    const Ctrl* ctrl = reinterpret_cast<const Ctrl*>(P0.ws + P0.wl.ctrl);
+    if (cudaMemcpyAsync(&B, &ctrl->auto_B, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return NUMARCK_ERR_CUDA;
+    if (B < 1 || B > NUMARCK_MAX_B) return NUMARCK_ERR_CUDA;
+    numarck_params q{};
+    q.dtype = P0.g.dtype;
+    q.B = B;
+    q.E = P0.hdr.E;
+    q.anchor = P0.g.anchor;
+    q.block_bytes = P0.hdr.block_bytes;
+    size_t cap = (size_t)(P0.g.off_exact + P0.g.n * (P0.g.dtype == NUMARCK_F64 ? 8 : 4));
+    const int rc = plan_compress(P0.prev, P0.cur, P0.g.n, &q, P0.blob, cap, P0.ws, P0.wl.total, &P);
+    if (rc) return rc;
+    P.sms = P0.sms;
+    P.code_off = P0.code_off;
+  }
   if (launch_topk(P, s) != cudaSuccess) return NUMARCK_ERR_CUDA;
   trace(2, 6, s);
   if (launch_assign(P, s) != cudaSuccess) return NUMARCK_ERR_CUDA;
@@ -290,6 +333,12 @@ int numarck_compress(const void* prev, const void* cur, int64_t n, const numarck
   CompressPlan P;
   const int rc = plan_compress(prev, cur, n, p, blob, blob_cap, ws, ws_bytes, &P);
   if (rc) return rc;
+  if (P.auto_b) {   // choosing B synchronises the stream once: not allowed while capturing
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(reinterpret_cast<cudaStream_t>(stream), &cs) != cudaSuccess)
+      return NUMARCK_ERR_CUDA;
+    if (cs != cudaStreamCaptureStatusNone) return NUMARCK_ERR_INVALID_ARG;
+  }
   P.sms = device_sms();
   if (P.sms <= 0) return NUMARCK_ERR_CUDA;
   return launch_compress(P, reinterpret_cast<cudaStream_t>(stream));

@@ -59,7 +59,8 @@ struct Ctrl {
   unsigned int win_err;         // a bin fell outside the histogram window (never expected)
   int code_base;                // bin of code 0 in K1's per-point codes (written by K1)
   int sel_lo, sel_hi;           // bin range of the selected bins (sel_lo > sel_hi: none)
-  unsigned int pad1[46];
+  int auto_B;                   // index length chosen from the histogram (B = 0 requests)
+  unsigned int pad1[45];
 };
 static_assert(sizeof(Ctrl) == 256, "Ctrl must be 256 bytes");
 

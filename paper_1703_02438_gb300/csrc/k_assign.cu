@@ -452,7 +452,7 @@ constexpr int K3X_SMEM = K3X_WARPS * SUB * 2;   // per warp: up to SUB u16 posit
 template <typename T>
 __global__ void __launch_bounds__(K3X_THREADS) k3_exact(const T* __restrict__ cur,
                                                         const unsigned short* codes, Geometry g,
-                                                        unsigned char* blob) {
+                                                        unsigned char* blob, long long code_off) {
   extern __shared__ __align__(16) unsigned short k3x_list[];
   using U = typename Bits<T>::U;
   const int lane = (int)lane_id();
@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(K3X_THREADS) k3_exact(const T* __restrict__ cu
   const U* xu = reinterpret_cast<const U*>(cur);
   const long long L = (long long)sizeof(T);
   const long long n_inc = reinterpret_cast<const numarck_header*>(blob)->n_inc;
-  const bool from_codes = g.off_exact + n_inc * L <= code_offset(g);
+  const bool from_codes = g.off_exact + n_inc * L <= code_off;
   const int B = g.B;
   const unsigned M = (unsigned)g.M, fmask = (1u << B) - 1u;
   for (long long gt = (long long)blockIdx.x * K3X_WARPS + (threadIdx.x >> 5); gt < g.nsub;
@@ -571,7 +571,7 @@ static cudaError_t launch_assign_t(const CompressPlan& P, cudaStream_t s, const 
   A.cftab = reinterpret_cast<const float*>(P.ws + P.wl.cftab);
   A.tstatus = reinterpret_cast<unsigned long long*>(P.ws + P.wl.status);
   A.blob = P.blob;
-  A.codes = reinterpret_cast<const unsigned short*>(P.blob + code_offset(P.g));
+  A.codes = reinterpret_cast<const unsigned short*>(P.blob + P.code_off);
   static const std::array<K3Fn<T>, NUMARCK_MAX_B> table =
       k3_table<T>(std::make_integer_sequence<int, NUMARCK_MAX_B>{});
   if (P.g.B < 1 || P.g.B > NUMARCK_MAX_B) return cudaErrorInvalidValue;
@@ -631,9 +631,9 @@ static cudaError_t launch_exact_t(const CompressPlan& P, cudaStream_t s) {
   long long blocks = (long long)P.sms * per_sm;
   const long long need = (P.g.nsub + K3X_WARPS - 1) / K3X_WARPS;
   if (blocks > need) blocks = need;
-  const unsigned short* codes = reinterpret_cast<const unsigned short*>(P.blob + code_offset(P.g));
+  const unsigned short* codes = reinterpret_cast<const unsigned short*>(P.blob + P.code_off);
   k3_exact<T><<<(int)blocks, K3X_THREADS, K3X_SMEM, s>>>(static_cast<const T*>(P.cur), codes, P.g,
-                                                          P.blob);
+                                                          P.blob, (long long)P.code_off);
   return cudaGetLastError();
 }
 

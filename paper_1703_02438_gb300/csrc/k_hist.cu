@@ -363,7 +363,7 @@ cudaError_t launch_hist_tv(const CompressPlan& P, cudaStream_t s) {
   k1_hist<T, VEC><<<blocks, K1_THREADS, smem, s>>>(
       static_cast<const T*>(P.prev), static_cast<const T*>(P.cur), P.g.n, consts_of<T>(P),
       P.g.anchor == NUMARCK_ANCHOR_MIN ? 1 : 0, ctrl, hist, tstat, P.g.nsub,
-      reinterpret_cast<unsigned short*>(P.blob + code_offset(P.g)));
+      reinterpret_cast<unsigned short*>(P.blob + P.code_off));
   return cudaGetLastError();
 }
 

@@ -7,6 +7,9 @@
 // range takes every bin with count > T and the lowest-numbered bins with count == T
 // (ties go to the smaller bin id), and a second scan numbers the selected bins in ascending
 // bin order. The CTA also restores the workspace invariant (histogram and keys back to 0).
+//
+// k2_auto_b, for B = 0, chooses the index length from the same histogram before K2 runs
+// (§IV.B.2, Eqs. 5 and 6); it only reads the histogram.
 #include "launch.h"
 
 namespace nmk {
@@ -90,6 +93,135 @@ __device__ __forceinline__ unsigned long long block_max_ull(unsigned long long v
   return r;
 }
 
+// k-th largest of the non-zero values H[0..R) (k >= 1, more than k non-zero values, mx = the
+// largest value): *thr = that value and *need = how many values equal to it the k largest
+// include. Radix select, 8 bits per pass from the top bit of mx; called by all K2_THREADS.
+__device__ __forceinline__ void select_kth_largest(const unsigned long long* H, int R, long long k,
+                                                   unsigned long long mx, unsigned int* s_dig,
+                                                   unsigned long long* s_prefix,
+                                                   long long* s_rem, unsigned long long* thr,
+                                                   long long* need) {
+  const int tid = (int)threadIdx.x;
+  const int top = 63 - __clzll((long long)mx);
+  unsigned long long prefix = 0;
+  long long rem = k;
+  for (int shift = (top / 8) * 8; shift >= 0; shift -= 8) {
+    for (int i = tid; i < 256; i += K2_THREADS) s_dig[i] = 0u;
+    __syncthreads();
+    for (int i = tid; i < R; i += K2_THREADS) {
+      const unsigned long long v = H[i];
+      if (v != 0 && (shift + 8 >= 64 || (v >> (shift + 8)) == (prefix >> (shift + 8))))
+        atomicAdd(&s_dig[(v >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      long long cum = 0;
+      for (int d = 255; d >= 0; --d) {
+        if (cum + (long long)s_dig[d] >= rem) {
+          *s_prefix = prefix | ((unsigned long long)d << shift);
+          *s_rem = rem - cum;
+          break;
+        }
+        cum += s_dig[d];
+      }
+    }
+    __syncthreads();
+    prefix = *s_prefix;
+    rem = *s_rem;
+    __syncthreads();
+  }
+  *thr = prefix;
+  *need = rem;
+}
+
+// Automatic index length (§IV.B.2, Eqs. 5 and 6), one CTA after K1: for B = 1..16 the
+// compressible points are those in the top k = 2^B - 1 bins of the histogram, alpha(B) =
+// (n - compressible) / n, and 8 * file_size(B) = 8 * 2^B * L + n * B + 8 * L * n * alpha(B)
+// (exact integers); the smallest wins (ties: smaller B) and is written to ctrl->auto_B. The sum
+// of the top k counts for every k <= 65535 follows from the counts above the 65535-th largest
+// (compacted into `list`, fewer than 65535 of them) plus copies of that count.
+struct AutoArgs {
+  Ctrl* ctrl;
+  const unsigned long long* hist;
+  unsigned long long* list;     // scratch, 65536 entries
+  int hbase;
+  long long n;
+  int L;
+};
+
+__global__ void __launch_bounds__(K2_THREADS, 1) k2_auto_b(AutoArgs A) {
+  __shared__ long long s_ll[33];
+  __shared__ unsigned long long s_ull[33];
+  __shared__ unsigned int s_dig[256];
+  __shared__ unsigned long long s_prefix;
+  __shared__ long long s_rem;
+  __shared__ int s_m;
+  Ctrl* ctrl = A.ctrl;
+  const int tid = (int)threadIdx.x;
+  const unsigned kmin = ctrl->bmin_key, kmax = ctrl->bmax_key;
+  const int any = kmax != 0u;
+  const int bmin = any ? (int)(KEY_BIAS - kmin) : 0;
+  const int bmax = any ? (int)(kmax - KEY_BIAS) : -1;
+  int R = bmax - bmin + 1;
+  const int i0 = bmin - A.hbase;
+  if (any && (i0 < 0 || i0 + R > HWIN || ctrl->win_err)) R = 0;   // K2 reports the error
+  const unsigned long long* H = A.hist + (any ? i0 : 0);
+  constexpr long long KTOP = (1LL << NUMARCK_MAX_B) - 1;
+
+  long long nnz = 0;
+  unsigned long long mx = 0;
+  for (int i = tid; i < R; i += K2_THREADS) {
+    const unsigned long long v = H[i];
+    nnz += v != 0;
+    mx = v > mx ? v : mx;
+  }
+  nnz = block_sum_ll(nnz, s_ll);
+  mx = block_max_ull(mx, s_ull);
+  unsigned long long tmax = 0;   // the KTOP-th largest count (0 when at most KTOP bins)
+  long long need_max = 0;
+  if (nnz > KTOP) select_kth_largest(H, R, KTOP, mx, s_dig, &s_prefix, &s_rem, &tmax, &need_max);
+  if (tid == 0) s_m = 0;
+  __syncthreads();
+  for (int i = tid; i < R; i += K2_THREADS) {
+    const unsigned long long v = H[i];
+    if (v > tmax) A.list[atomicAdd(&s_m, 1)] = v;
+  }
+  __syncthreads();
+  const int m = s_m;                               // counts above tmax (fewer than KTOP)
+  unsigned long long lmx = 0;
+  long long lsum = 0;
+  for (int i = tid; i < m; i += K2_THREADS) {
+    lsum += (long long)A.list[i];
+    lmx = A.list[i] > lmx ? A.list[i] : lmx;
+  }
+  lsum = block_sum_ll(lsum, s_ll);
+  lmx = block_max_ull(lmx, s_ull);
+  const long long n = A.n, L = A.L;
+  long long best_bits = -1;
+  int best_B = 1;
+  for (int B = 1; B <= NUMARCK_MAX_B; ++B) {
+    const long long k = (1LL << B) - 1;
+    long long cov;
+    if (k >= m) {
+      cov = lsum + (k - m) * (long long)tmax;      // k - m <= need_max copies of tmax
+    } else {
+      unsigned long long t = 0;
+      long long need = 0;
+      select_kth_largest(A.list, m, k, lmx, s_dig, &s_prefix, &s_rem, &t, &need);
+      long long above = 0;
+      for (int i = tid; i < m; i += K2_THREADS) above += A.list[i] > t ? (long long)A.list[i] : 0;
+      cov = block_sum_ll(above, s_ll) + need * (long long)t;
+    }
+    const long long bits = 8 * (1LL << B) * L + n * B + 8 * L * (n - cov);
+    if (best_bits < 0 || bits < best_bits) {
+      best_bits = bits;
+      best_B = B;
+    }
+  }
+  (void)need_max;
+  if (tid == 0) ctrl->auto_B = best_B;
+}
+
 template <typename T>
 __device__ __forceinline__ T anchor_value(const Ctrl* ctrl, const Consts<T>& c, int anchor) {
   if (anchor != NUMARCK_ANCHOR_MIN) return c.a;
@@ -138,38 +270,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_topk(TopkArgs A, Consts<T> c
   // radix select of the k-th largest count (when more than k bins are non-empty)
   unsigned long long thr = 0;  // select count > thr, plus `need` bins with count == thr
   long long need = 0;
-  if (nnz > k) {
-    const int top = 63 - __clzll((long long)mx);
-    unsigned long long prefix = 0;
-    long long rem = k;
-    for (int shift = (top / 8) * 8; shift >= 0; shift -= 8) {
-      for (int i = tid; i < 256; i += K2_THREADS) s_dig[i] = 0u;
-      __syncthreads();
-      for (int i = tid; i < R; i += K2_THREADS) {
-        const unsigned long long v = H[i];
-        if (v != 0 && (shift + 8 >= 64 || (v >> (shift + 8)) == (prefix >> (shift + 8))))
-          atomicAdd(&s_dig[(v >> shift) & 255u], 1u);
-      }
-      __syncthreads();
-      if (tid == 0) {
-        long long cum = 0;
-        for (int d = 255; d >= 0; --d) {
-          if (cum + (long long)s_dig[d] >= rem) {
-            s_prefix = prefix | ((unsigned long long)d << shift);
-            s_rem = rem - cum;
-            break;
-          }
-          cum += s_dig[d];
-        }
-      }
-      __syncthreads();
-      prefix = s_prefix;
-      rem = s_rem;
-      __syncthreads();
-    }
-    thr = prefix;
-    need = rem;
-  }
+  if (nnz > k) select_kth_largest(H, R, k, mx, s_dig, &s_prefix, &s_rem, &thr, &need);
 
   // ordered scans over the bin range: ties in count go to the smaller bin, then ranks
   int tie_base = 0, rank_base = 0;
@@ -269,6 +370,18 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_topk(TopkArgs A, Consts<T> c
 }
 
 }  // namespace
+
+cudaError_t launch_auto_b(const CompressPlan& P, cudaStream_t s) {
+  AutoArgs A;
+  A.ctrl = reinterpret_cast<Ctrl*>(P.ws + P.wl.ctrl);
+  A.hist = reinterpret_cast<const unsigned long long*>(P.ws + P.wl.hist);
+  A.list = reinterpret_cast<unsigned long long*>(P.ws + P.wl.mtab);   // filled by K2 later
+  A.hbase = P.g.dtype == NUMARCK_F64 ? P.cd.hbase : P.cf.hbase;
+  A.n = P.g.n;
+  A.L = P.g.dtype == NUMARCK_F64 ? 8 : 4;
+  k2_auto_b<<<1, K2_THREADS, 0, s>>>(A);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_topk(const CompressPlan& P, cudaStream_t s) {
   TopkArgs A;

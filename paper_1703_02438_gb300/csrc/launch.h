@@ -18,6 +18,8 @@ struct CompressPlan {
   Consts<double> cd;       // valid when dtype == F64
   bool aligned16;          // prev and cur both 16-byte aligned
   int sms;                 // multiprocessors of the current device
+  int64_t code_off;        // byte offset of K1's per-point codes in the blob buffer
+  bool auto_b;             // B = 0: choose B from the histogram (§IV.B.2) after K1
 };
 
 // Decompression of elements [start, start+count). The kernel takes the blob's geometry from the
@@ -35,6 +37,7 @@ struct DecodePlan {
 
 cudaError_t launch_anchor_min(const CompressPlan& P, cudaStream_t s);  // K0 (ANCHOR_MIN only)
 cudaError_t launch_hist(const CompressPlan& P, cudaStream_t s);        // K1
+cudaError_t launch_auto_b(const CompressPlan& P, cudaStream_t s);      // B from the histogram
 cudaError_t launch_topk(const CompressPlan& P, cudaStream_t s);        // K2
 cudaError_t launch_assign(const CompressPlan& P, cudaStream_t s);      // K3a: indices + packing
 cudaError_t launch_offsets(const CompressPlan& P, cudaStream_t s);     // K3b: offset tables

@@ -53,6 +53,38 @@ class BatchItem(ctypes.Structure):
                 ("params", Params), ("blob", ctypes.c_void_p), ("blob_cap", ctypes.c_size_t)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_size_t),
+                ("slots", ctypes.c_int32), ("max_series", ctypes.c_int32),
+                ("dry_run", ctypes.c_int32), ("dry_run_us", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("series", ctypes.c_int32), ("params", Params),
+                ("n", ctypes.c_int64), ("host_in", ctypes.c_void_p), ("host_out", ctypes.c_void_p),
+                ("host_out_cap", ctypes.c_size_t), ("start", ctypes.c_int64),
+                ("count", ctypes.c_int64)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("series", ctypes.c_int32), ("reference", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("out_bytes", ctypes.c_uint64), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_end", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("started", ctypes.c_uint64),
+                ("completed", ctypes.c_uint64), ("deferred_memory", ctypes.c_uint64),
+                ("arena_bytes", ctypes.c_uint64), ("arena_used", ctypes.c_uint64),
+                ("arena_peak", ctypes.c_uint64), ("max_inflight", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("now", ctypes.c_double)]
+
+
+REQ_COMPRESS = 0
+REQ_DECOMPRESS = 1
+
+
 class BatchDecodeItem(ctypes.Structure):
     _fields_ = [("blob", ctypes.c_void_p), ("prev", ctypes.c_void_p), ("out", ctypes.c_void_p),
                 ("n", ctypes.c_int64)]
@@ -102,6 +134,18 @@ def lib() -> ctypes.CDLL:
         L.numarck_compress_noalloc.restype = i32
         L.numarck_version.argtypes = []
         L.numarck_version.restype = ctypes.c_char_p
+        L.numarck_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(i32)]
+        L.numarck_server_create.restype = vp
+        L.numarck_server_submit.argtypes = [vp, ctypes.POINTER(Request),
+                                            ctypes.POINTER(ctypes.c_uint64)]
+        L.numarck_server_submit.restype = i32
+        L.numarck_server_poll.argtypes = [vp, ctypes.POINTER(Completion), i32, ctypes.POINTER(i32),
+                                          i32]
+        L.numarck_server_poll.restype = i32
+        L.numarck_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+        L.numarck_server_get_stats.restype = i32
+        L.numarck_server_destroy.argtypes = [vp]
+        L.numarck_server_destroy.restype = i32
         _lib = L
     return _lib
 
@@ -322,3 +366,65 @@ def trace_events(events) -> None:
 
 def version() -> str:
     return lib().numarck_version().decode()
+
+
+class Server:
+    """The served form (numarck_server_*): a request loop over resident time series in one
+    device arena. Host buffers passed to submit() must be pinned and stay alive until their
+    completion is polled (this object keeps a reference until then)."""
+
+    def __init__(self, arena: torch.Tensor | None, slots: int = 8, max_series: int = 64,
+                 dry_run_us: int | None = None, arena_bytes: int | None = None):
+        size = arena.numel() if arena is not None else (arena_bytes or (1 << 40))
+        cfg = ServerConfig(ctypes.c_void_p(arena.data_ptr() if arena is not None else 0), size,
+                           int(slots),
+                           int(max_series), 1 if dry_run_us is not None else 0,
+                           int(dry_run_us or 0))
+        st = ctypes.c_int32(0)
+        self._arena = arena
+        self._h = lib().numarck_server_create(ctypes.byref(cfg), ctypes.byref(st))
+        if not self._h:
+            raise NumarckError(st.value, "numarck_server_create")
+        self._keep = {}
+
+    def submit(self, kind: int, series: int, n: int, params: Params | None = None,
+               host_in: torch.Tensor | None = None, host_out: torch.Tensor | None = None,
+               start: int = 0, count: int | None = None) -> int:
+        r = Request(int(kind), int(series), params or Params(), int(n),
+                    ctypes.c_void_p(host_in.data_ptr() if host_in is not None else 0),
+                    ctypes.c_void_p(host_out.data_ptr() if host_out is not None else 0),
+                    host_out.numel() * host_out.element_size() if host_out is not None else 0,
+                    int(start), int(n - start if count is None else count))
+        rid = ctypes.c_uint64(0)
+        _check(lib().numarck_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid)),
+               "numarck_server_submit")
+        self._keep[rid.value] = (host_in, host_out)
+        return rid.value
+
+    def poll(self, max_items: int = 256, wait_ms: int = 0) -> list:
+        arr = (Completion * max_items)()
+        got = ctypes.c_int32(0)
+        _check(lib().numarck_server_poll(self._h, arr, max_items, ctypes.byref(got), int(wait_ms)),
+               "numarck_server_poll")
+        out = []
+        for i in range(got.value):
+            c = arr[i]
+            self._keep.pop(c.id, None)
+            out.append({f: getattr(c, f) for f, _ in Completion._fields_ if f != "pad"})
+        return out
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().numarck_server_get_stats(self._h, ctypes.byref(st)), "numarck_server_get_stats")
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_ if f != "pad"}
+
+    def close(self) -> None:
+        if self._h:
+            h, self._h = self._h, None
+            _check(lib().numarck_server_destroy(h), "numarck_server_destroy")
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

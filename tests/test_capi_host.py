@@ -54,7 +54,7 @@ def test_compress_bound_matches_format(lib, dtype, T, B, n):
 
 
 def test_invalid_params_rejected(lib):
-    bad = [N.Params(2, 8, 1e-3, 0, 0, 0), N.Params(0, 0, 1e-3, 0, 0, 0),
+    bad = [N.Params(2, 8, 1e-3, 0, 0, 0), N.Params(0, -1, 1e-3, 0, 0, 0),
            N.Params(0, 17, 1e-3, 0, 0, 0), N.Params(0, 8, 0.0, 0, 0, 0),
            N.Params(0, 8, 1.0, 0, 0, 0), N.Params(0, 8, float("nan"), 0, 0, 0),
            N.Params(0, 8, 2.0 ** -61, 0, 0, 0), N.Params(0, 8, 1e-3, 2, 0, 0),
@@ -65,6 +65,29 @@ def test_invalid_params_rejected(lib):
         assert N.workspace_bytes(10, p) == 0
     good = N.Params(0, 8, 1e-3, 0, 0, 0)
     assert N.compress_bound(-1, good) == 0 and N.compress_bound((1 << 40) + 1, good) == 0
+
+
+def test_automatic_B_is_sized_for_every_layout(lib):
+    """B = 0 (chosen from the histogram, §IV.B.2) needs room for any B = 1..16: the blob bound
+    and the workspace are the largest over B (a smaller B can have more sub-blocks: every
+    index block ends in a partial tile)."""
+    for dtype, T in ((N.F64, np.float64), (N.F32, np.float32)):
+        for n in (0, 1, 4097, 3_000_001, 1 << 30):
+            auto = N.Params(dtype, 0, 1e-3, 0, 0, 0)
+            each = [N.Params(dtype, B, 1e-3, 0, 0, 0) for B in range(1, 17)]
+            assert N.compress_bound(n, auto) == O.compress_bound(n, T, 0)
+            assert N.compress_bound(n, auto) == max(N.compress_bound(n, p) for p in each)
+            assert N.workspace_bytes(n, auto) == max(N.workspace_bytes(n, p) for p in each)
+    # at 2^30 elements B = 6 has more sub-blocks than B = 16
+    big = 1 << 30
+    assert (N.workspace_bytes(big, N.Params(N.F64, 6, 1e-3, 0, 0, 0))
+            > N.workspace_bytes(big, N.Params(N.F64, 16, 1e-3, 0, 0, 0)))
+
+
+def test_batch_rejects_automatic_B(lib):
+    item = N.BatchItem(None, None, 1000, N.Params(N.F64, 0, 1e-3, 0, 0, 0), None, 0)
+    arr = (N.BatchItem * 1)(item)
+    assert lib.numarck_batch_workspace_bytes(arr, 1, 1) == 0
 
 
 def test_compress_argument_errors_before_device(lib):

@@ -6,6 +6,8 @@ the whole blob (header, centre table, offset tables, index blocks, incompressibl
 byte-identical to the oracle's, and decompression bit-identical. Inputs are the seeded synthetic
 workloads (scaled and full size) plus adversarial cases.
 """
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -297,3 +299,58 @@ def test_check_boundary_near_and_far_bins(T, E, anchor):
     p, x = _check_boundary_pair(T, E)
     h, _ = check_pair(p, x, E, 8, anchor=anchor)
     assert 0 < h["n_inc"] < h["n"]
+
+
+# ---------------------------------------------------------------------------------------
+# automatic index length (B = 0, §IV.B.2)
+# ---------------------------------------------------------------------------------------
+def _many_bins_pair(n=1 << 21, seed=31):
+    """Ratios spread over about 470000 bins of width 2^-19: more than 65535 non-empty bins."""
+    rng = np.random.default_rng(seed)
+    p = rng.lognormal(size=n)
+    return p, p * (1.0 + rng.uniform(-0.45, 0.45, n))
+
+
+@pytest.mark.parametrize("case", ["plain", "plain_min", "climate", "flash", "many_bins"])
+def test_auto_B_matches_oracle(case):
+    anchor = N.ANCHOR_MIN if case == "plain_min" else N.ANCHOR_ZERO
+    if case.startswith("plain"):
+        p, x = synth.plain_pair(1 << 20, seed=synth.seed_for(0, 41))
+        p, x, E = p.numpy(), x.numpy(), 1e-3
+    elif case == "climate":
+        (_, a), (_, b) = list(synth.climate_series(360, 720, steps=2))
+        p, x, E = a.numpy(), b.numpy(), 1e-3
+    elif case == "flash":
+        xs = synth.flash_series(side=64, steps=2)
+        p, x, E = xs[0].numpy(), xs[1].numpy(), 1e-4
+    else:
+        p, x = _many_bins_pair()
+        E = 2.0 ** -20
+    h, _ = check_pair(p, x, E, 0, anchor=anchor, ranges=[(1000, 5000)])
+    bins, counts = O.histogram(*_oracle_bins(p, x, E, anchor))
+    assert h["B"] == O.choose_B(counts, p.size, p.dtype.itemsize)
+
+
+def _oracle_bins(p, x, E, anchor):
+    T = p.dtype.type
+    E_T, w, inv_w, cap = O.grid_constants(T, E)
+    ratio, binnable = O.change_ratio(p, x, cap)
+    a = O.grid_anchor(ratio, binnable, E_T, anchor)
+    return O.bin_ids(ratio, binnable, a, inv_w), binnable
+
+
+@pytest.mark.filterwarnings("ignore:The CUDA Graph is empty")
+def test_auto_B_refused_while_capturing():
+    p, x = synth.plain_pair(4096, seed=synth.seed_for(0, 42))
+    pd, xd = p.to(DEV), x.to(DEV)
+    params = N.make_params(torch.float64, 0, 1e-3)
+    blob = torch.empty(N.compress_bound(4096, params), dtype=torch.uint8, device=DEV)
+    ws = torch.zeros(N.workspace_bytes(4096, params), dtype=torch.uint8, device=DEV)
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    rc = None
+    with torch.cuda.graph(graph, stream=s):
+        rc = N.lib().numarck_compress(pd.data_ptr(), xd.data_ptr(), 4096, ctypes.byref(params),
+                                      blob.data_ptr(), blob.numel(), ws.data_ptr(), ws.numel(),
+                                      s.cuda_stream)
+    assert rc == N.ERR_INVALID_ARG

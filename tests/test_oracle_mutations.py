@@ -34,6 +34,9 @@ PINS = [
     P.test_offsets_tables_are_prefix_counts,
     P.test_decompress_closed_form,
     P.test_decompress_range_equals_slice,
+    P.test_file_size_hand_example,
+    P.test_choose_B_single_bin_and_uniform_bins,
+    P.test_choose_B_tie_goes_to_smaller_B,
 ]
 
 
@@ -141,6 +144,26 @@ def _hist_counts_all(b, binnable):
     return bins.astype(np.int64), counts.astype(np.int64)
 
 
+def _sizes_k_is_2_pow_B(counts, n, L, B_max=16):
+    desc = np.sort(np.asarray(counts, dtype=np.int64))[::-1]
+    prefix = np.concatenate([[0], np.cumsum(desc, dtype=np.int64)])
+    return [8 * (1 << B) * L + n * B + 8 * L * (n - int(prefix[min(1 << B, desc.size)]))
+            for B in range(1, B_max + 1)]
+
+
+def _choose_B_ties_to_larger(counts, n, L, B_max=16):
+    bits = O.file_size_bits(counts, n, L, B_max)
+    m = min(bits)
+    return max(i + 1 for i, v in enumerate(bits) if v == m)
+
+
+def _sizes_index_term_in_bytes_per_bit(counts, n, L, B_max=16):
+    desc = np.sort(np.asarray(counts, dtype=np.int64))[::-1]
+    prefix = np.concatenate([[0], np.cumsum(desc, dtype=np.int64)])
+    return [8 * (1 << B) * L + 8 * n * B + 8 * L * (n - int(prefix[min((1 << B) - 1, desc.size)]))
+            for B in range(1, B_max + 1)]
+
+
 MUTATIONS = {
     "ratio divides by cur": ("change_ratio", _ratio_over_cur),
     "ratio sign flipped": ("change_ratio", _ratio_wrong_sign),
@@ -155,6 +178,9 @@ MUTATIONS = {
     "elements per block off by one": ("elements_per_block", _epb_plus_one),
     "bin width E instead of 2E": ("grid_constants", _grid_width_E),
     "histogram counts non-binnable points": ("histogram", _hist_counts_all),
+    "auto-B top 2^B bins": ("file_size_bits", _sizes_k_is_2_pow_B),
+    "auto-B ties to the larger B": ("choose_B", _choose_B_ties_to_larger),
+    "auto-B index table in bytes per bit": ("file_size_bits", _sizes_index_term_in_bytes_per_bit),
 }
 
 

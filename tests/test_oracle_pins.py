@@ -470,3 +470,43 @@ def test_metrics_against_paper_examples():
     assert abs(O.mean_error_rate(cur, rec) - 0.3 / 4) < 1e-15
     # Eq. 5: alpha = (n - compressible) / n
     assert O.incompressible_ratio(200, 150) == 0.25
+
+
+# ---------------------------------------------------------------------------------------
+# Automatic index length (§IV.B.2, Eqs. 5 and 6), reading R10
+# ---------------------------------------------------------------------------------------
+def test_file_size_hand_example():
+    """Six bins holding 600, 200, 100, 50, 30, 20 of n = 1000 float64 points. By hand, in bytes:
+    B=1: 2*8 + 1000/8 + 400*8 = 3341; B=2: 32 + 250 + 100*8 = 1082; B=3: 64 + 375 + 0 = 439;
+    B=4: 128 + 500 = 628; B=5: 256 + 625 = 881. The smallest is B = 3."""
+    counts = np.array([30, 600, 20, 100, 200, 50])
+    bits = O.file_size_bits(counts, 1000, 8, B_max=5)
+    assert bits == [8 * 3341, 8 * 1082, 8 * 439, 8 * 628, 8 * 881]
+    assert O.choose_B(counts, 1000, 8) == 3
+
+
+def test_choose_B_single_bin_and_uniform_bins():
+    # every point in one bin: the 1-bit table already covers it, B = 1
+    assert O.choose_B(np.array([10 ** 6]), 10 ** 6, 8) == 1
+    # 15 equal bins of 10^4 float32 points: B = 4 covers them all (64 + 75000 bytes);
+    # B = 3 leaves 8 bins out (32 + 56250 + 80000 * 4), B = 5 doubles the table (128 + 93750)
+    assert O.choose_B(np.full(15, 10 ** 4), 150_000, 4) == 4
+
+
+def test_choose_B_tie_goes_to_smaller_B():
+    """n = 96 float32 points: one bin of 80, bins of 3 and 2, eleven bins of 1. In bits,
+    B=1: 64 + 96 + 32 * 16 = 672 and B=2: 128 + 192 + 32 * 11 = 672 tie; B=3 is 768."""
+    counts = np.array([80, 3, 2] + [1] * 11)
+    bits = O.file_size_bits(counts, 96, 4, B_max=3)
+    assert bits == [672, 672, 768]
+    assert O.choose_B(counts, 96, 4) == 1
+
+
+def test_auto_B_blob_equals_the_chosen_B():
+    rng = np.random.default_rng(21)
+    p = rng.lognormal(size=20_000)
+    x = p * (1 + rng.normal(0, 3e-3, p.size))
+    auto = O.compress(p, x, 1e-3, 0)
+    B = O.parse_header(auto.to_bytes())["B"]
+    assert 1 <= B <= 16
+    assert auto.to_bytes() == O.compress(p, x, 1e-3, B).to_bytes()
