@@ -346,6 +346,54 @@ const char* numarck_status_string(int code);
 /* Library version string, e.g. "numarck-gb300 1 sm_103a". */
 const char* numarck_version(void);
 
+/* ---- lossless index compression (§IV.C: each index block compressed with ZLIB) ----
+ *
+ * numarck_deflate_index turns a blob's index section into a container of zlib streams (RFC
+ * 1950; DEFLATE data of RFC 1951 that any inflater, e.g. zlib's, reads): one stream per index
+ * block holding the block's ceil(count * B / 8) bytes (without the raw blob's 16-byte padding).
+ * Inside a stream each 4096-element sub-block is one fixed-Huffman DEFLATE block whose matches
+ * stay inside the sub-block, followed by an empty stored block that ends it on a byte boundary,
+ * so any sub-block inflates on its own: numarck_inflate_index restores only the sub-blocks that
+ * cover [start, start + count) into a blob buffer (the raw index section, padding included),
+ * which numarck_decompress_range then decodes.
+ *
+ * Container (little-endian): numarck_zindex_header (64 bytes) · int64 zoff[nblocks + 1] at
+ * off_zoff (byte offset of index block q's zlib stream; the last entry = total_bytes) · int64
+ * sub_zoff[nsub] at off_sub_zoff (byte offset of sub-block t's DEFLATE data) · the streams from
+ * off_data on. */
+#define NUMARCK_ZINDEX_MAGIC        0x5849414Eu   /* "NAIX" */
+#define NUMARCK_ZINDEX_HEADER_BYTES 64
+
+typedef struct numarck_zindex_header {
+  uint32_t magic;        /*   0 */
+  int32_t  version;      /*   4: 1 */
+  int32_t  B;            /*   8 */
+  int32_t  pad;          /*  12 */
+  int64_t  n;            /*  16 */
+  int64_t  nblocks;      /*  24 */
+  int64_t  nsub;         /*  32 */
+  int64_t  off_zoff;     /*  40 */
+  int64_t  off_sub_zoff; /*  48 */
+  int64_t  off_data;     /*  56; the container's size is zoff[nblocks]                     */
+} numarck_zindex_header;
+
+/* Bytes a container can need for the blob whose header (host copy) is given; 0 if invalid. */
+size_t numarck_zindex_bound(const void* blob_header_host);
+/* Device workspace bytes numarck_deflate_index needs (16 per sub-block); 0 if invalid. */
+size_t numarck_zindex_workspace_bytes(const void* blob_header_host);
+/* Deflates the index section of a compressed blob (device, with its header's host copy) into
+ * zindex (device, zcap >= numarck_zindex_bound, 256-byte aligned). Asynchronous on stream;
+ * the container's size is zoff[nblocks] (the 8 bytes at off_zoff + 8 * nblocks). */
+int numarck_deflate_index(const void* blob, const void* blob_header_host, void* zindex,
+                          size_t zcap, void* ws, size_t ws_bytes, numarck_stream_t stream);
+/* Inflates the sub-blocks that cover elements [start, start + count) from a container (device,
+ * zbytes long) into the index section of `blob` (device, laid out as blob_header_host says;
+ * the other sections are not touched). Malformed data sets *status_dev (if non-NULL) to
+ * NUMARCK_ERR_CORRUPT. Asynchronous on stream. */
+int numarck_inflate_index(const void* zindex, size_t zbytes, const void* blob_header_host,
+                          void* blob, int64_t start, int64_t count, int32_t* status_dev,
+                          numarck_stream_t stream);
+
 /* ---- served form: a request loop over resident time series (§I in-situ use, §IV.D) ----
  *
  * A server takes one caller-owned device buffer (the arena) and serves compress and

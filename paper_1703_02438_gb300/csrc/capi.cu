@@ -381,6 +381,82 @@ int numarck_trace_events(void* const* events, int count) {
   return NUMARCK_OK;
 }
 
+namespace {
+
+int blob_geometry(const void* header_host, Geometry* g) {
+  if (!header_host) return NUMARCK_ERR_INVALID_ARG;
+  numarck_header h;
+  std::memcpy(&h, header_host, sizeof(h));
+  return check_header(h, g);
+}
+
+}  // namespace
+
+size_t numarck_zindex_bound(const void* header_host) {
+  Geometry g;
+  if (blob_geometry(header_host, &g)) return 0;
+  return (size_t)zindex_bound(g);
+}
+
+size_t numarck_zindex_workspace_bytes(const void* header_host) {
+  Geometry g;
+  if (blob_geometry(header_host, &g)) return 0;
+  return (size_t)std::max<int64_t>(256, g.nsub * 16);
+}
+
+int numarck_deflate_index(const void* blob, const void* header_host, void* zindex, size_t zcap,
+                          void* ws, size_t ws_bytes, numarck_stream_t stream) {
+  Geometry g;
+  int rc = blob_geometry(header_host, &g);
+  if (rc) return rc;
+  if (!blob || !zindex || !ws || !aligned(blob, 256) || !aligned(zindex, 256) || !aligned(ws, 16))
+    return NUMARCK_ERR_INVALID_ARG;
+  if (zcap < (size_t)zindex_bound(g) || ws_bytes < (size_t)std::max<int64_t>(256, g.nsub * 16))
+    return NUMARCK_ERR_CAPACITY;
+  const int sms = device_sms();
+  if (sms <= 0) return NUMARCK_ERR_CUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (g.nsub == 0) {   // no index: the container is its header and one zoff entry
+    numarck_zindex_header zh;
+    zindex_layout(g, &zh);
+    static thread_local unsigned char img[NUMARCK_ZINDEX_HEADER_BYTES + 16];
+    std::memcpy(img, &zh, NUMARCK_ZINDEX_HEADER_BYTES);
+    const int64_t total = zh.off_data;
+    std::memcpy(img + NUMARCK_ZINDEX_HEADER_BYTES, &total, 8);
+    if (cudaMemcpyAsync(zindex, img, NUMARCK_ZINDEX_HEADER_BYTES + 8, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return NUMARCK_ERR_CUDA;
+    return NUMARCK_OK;
+  }
+  if (launch_deflate(static_cast<const unsigned char*>(blob), g,
+                     static_cast<unsigned char*>(zindex), static_cast<unsigned char*>(ws), sms,
+                     s) != cudaSuccess)
+    return NUMARCK_ERR_CUDA;
+  return NUMARCK_OK;
+}
+
+int numarck_inflate_index(const void* zindex, size_t zbytes, const void* header_host, void* blob,
+                          int64_t start, int64_t count, int32_t* status_dev,
+                          numarck_stream_t stream) {
+  Geometry g;
+  int rc = blob_geometry(header_host, &g);
+  if (rc) return rc;
+  if (!zindex || !blob || !aligned(zindex, 256) || !aligned(blob, 256))
+    return NUMARCK_ERR_INVALID_ARG;
+  if (start < 0 || count < 0 || start > g.n || count > g.n - start) return NUMARCK_ERR_RANGE;
+  if (count == 0) return NUMARCK_OK;
+  const int64_t first = start, last = start + count - 1;
+  const int64_t q0 = first / g.epb, q1 = last / g.epb;
+  const int64_t g0 = q0 * g.spb + (first - q0 * g.epb) / SUB;
+  const int64_t g1 = q1 * g.spb + (last - q1 * g.epb) / SUB;
+  if (launch_inflate(static_cast<const unsigned char*>(zindex), (long long)zbytes,
+                     static_cast<unsigned char*>(blob), g, g0, g1, status_dev,
+                     reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return NUMARCK_ERR_CUDA;
+  return NUMARCK_OK;
+}
+
 const char* numarck_status_string(int code) {
   switch (code) {
     case NUMARCK_OK: return "ok";

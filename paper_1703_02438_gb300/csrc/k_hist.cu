@@ -9,8 +9,8 @@
 //
 // The paper builds a local histogram per MPI rank and merges them with MPI_Allreduce (§IV.B.1).
 // Here each CTA keeps a private shared-memory histogram over a 16384-bin window around the
-// zero-change bin; lanes of a warp that hit the same bin are merged with match.any before one
-// shared atomic, and each CTA merges its window into the global histogram once at the end.
+// zero-change bin (one shared atomic per point), and each CTA merges its window into the
+// global histogram once at the end.
 // Bins outside the shared window go straight to the global window with one atomic.
 #include "launch.h"
 
@@ -74,27 +74,25 @@ __device__ __forceinline__ unsigned bin_code(const HistCtx& h, bool binned, int 
   return off < (unsigned)CODE_BINS ? (off << 1) | (pass ? 1u : 0u) : CODE_FAR;
 }
 
-// All 32 lanes call this together (valid may differ per lane). lt = lanes below this one. Bins
-// outside the shared window also update this thread's bin range (the range of the bins inside
-// it is read from the shared histogram at the end).
-__device__ __forceinline__ void hist_add(const HistCtx& h, bool valid, int b, unsigned lt,
-                                         int& lmin, int& lmax) {
-  const unsigned key = valid ? (unsigned)b : 0x80000000u;   // INT_MIN is never a bin
-  const unsigned peers = __match_any_sync(0xffffffffu, key);
-  if (valid && (peers & lt) == 0u) {                         // lowest lane of its group
-    const unsigned cnt = __popc(peers);
-    const int si = b - h.sbase;
-    if ((unsigned)si < (unsigned)SH_BINS) {
-      atomicAdd(&h.sh[si], cnt);
-    } else {
-      lmin = min(lmin, b);
-      lmax = max(lmax, b);
-      const int gi = b - h.hbase;
-      if ((unsigned)gi < (unsigned)HWIN)
-        atomicAdd(&h.hist[gi], (unsigned long long)cnt);
-      else
-        atomicOr(&h.ctrl->win_err, 1u);
-    }
+// One point of bin b into the histogram (if valid): a shared-memory atomic inside the shared
+// window (the hardware resolves lanes of a warp that hit the same bin; measured faster here
+// than aggregating them first with match.any, on concentrated and on spread bins alike), a
+// global one outside it. Bins outside the shared window also update this thread's bin range
+// (the range of the bins inside it is read from the shared histogram at the end).
+__device__ __forceinline__ void hist_add(const HistCtx& h, bool valid, int b, int& lmin,
+                                         int& lmax) {
+  if (!valid) return;
+  const int si = b - h.sbase;
+  if ((unsigned)si < (unsigned)SH_BINS) {
+    atomicAdd(&h.sh[si], 1u);
+  } else {
+    lmin = min(lmin, b);
+    lmax = max(lmax, b);
+    const int gi = b - h.hbase;
+    if ((unsigned)gi < (unsigned)HWIN)
+      atomicAdd(&h.hist[gi], 1ull);
+    else
+      atomicOr(&h.ctrl->win_err, 1u);
   }
 }
 
@@ -197,7 +195,6 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_hist(const T* __restrict__ p
 
   int lmin = 0x7FFFFFFF, lmax = (int)0x80000000;
   const int lane = (int)lane_id();
-  const unsigned lt = lanemask_lt();
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
 
@@ -232,7 +229,7 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_hist(const T* __restrict__ p
           const bool binned = kind == 1;
           if (kind >= 2) pend |= 1u << (u * V::N + v);
           cw[v] = bin_code(h, binned, b, pass);
-          hist_add(h, binned, b, lt, lmin, lmax);
+          hist_add(h, binned, b, lmin, lmax);
         }
         if (ok[u]) reinterpret_cast<typename V::codes*>(codes)[vi] = V::pack(cw);
       }
@@ -248,7 +245,7 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_hist(const T* __restrict__ p
           binned = Classifier<T>::exact(prev[j], cur[j], c, h.cbase, b, pass) == 1;
           codes[j] = (unsigned short)bin_code(h, binned, b, pass);
         }
-        hist_add(h, binned, b, lt, lmin, lmax);
+        hist_add(h, binned, b, lmin, lmax);
       }
     }
     // scalar tail (< V elements), one warp
@@ -261,7 +258,7 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_hist(const T* __restrict__ p
         binned = Classifier<T>::exact(ld_stream(prev + j), ld_stream(cur + j), c, h.cbase, b,
                                       pass) == 1;
       if (j < n) codes[j] = (unsigned short)bin_code(h, binned, b, pass);
-      hist_add(h, binned, b, lt, lmin, lmax);
+      hist_add(h, binned, b, lmin, lmax);
     }
   } else {
     constexpr int U = 8;
@@ -281,7 +278,7 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_hist(const T* __restrict__ p
         bool pass = false;
         const bool binned = ok[u] && Classifier<T>::exact(pe[u], xe[u], c, h.cbase, b, pass) == 1;
         if (ok[u]) codes[base + u * 32 + lane] = (unsigned short)bin_code(h, binned, b, pass);
-        hist_add(h, binned, b, lt, lmin, lmax);
+        hist_add(h, binned, b, lmin, lmax);
       }
     }
   }

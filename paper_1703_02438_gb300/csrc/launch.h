@@ -38,6 +38,15 @@ struct DecodePlan {
 cudaError_t launch_anchor_min(const CompressPlan& P, cudaStream_t s);  // K0 (ANCHOR_MIN only)
 cudaError_t launch_hist(const CompressPlan& P, cudaStream_t s);        // K1
 cudaError_t launch_auto_b(const CompressPlan& P, cudaStream_t s);      // B from the histogram
+// Lossless index compression (k_zlib.cu): container layout and bound for a blob's geometry,
+// deflate of every index block, inflate of sub-blocks [g0, g1].
+int zindex_layout(const Geometry& g, numarck_zindex_header* zh);
+int64_t zindex_bound(const Geometry& g);
+cudaError_t launch_deflate(const unsigned char* blob, const Geometry& g, unsigned char* z,
+                           unsigned char* ws, int sms, cudaStream_t s);
+cudaError_t launch_inflate(const unsigned char* z, long long zbytes, unsigned char* blob,
+                           const Geometry& g, long long g0, long long g1, int32_t* status,
+                           cudaStream_t s);
 cudaError_t launch_topk(const CompressPlan& P, cudaStream_t s);        // K2
 cudaError_t launch_assign(const CompressPlan& P, cudaStream_t s);      // K3a: indices + packing
 cudaError_t launch_offsets(const CompressPlan& P, cudaStream_t s);     // K3b: offset tables

@@ -134,6 +134,14 @@ def lib() -> ctypes.CDLL:
         L.numarck_compress_noalloc.restype = i32
         L.numarck_version.argtypes = []
         L.numarck_version.restype = ctypes.c_char_p
+        L.numarck_zindex_bound.argtypes = [vp]
+        L.numarck_zindex_bound.restype = sz
+        L.numarck_zindex_workspace_bytes.argtypes = [vp]
+        L.numarck_zindex_workspace_bytes.restype = sz
+        L.numarck_deflate_index.argtypes = [vp, vp, vp, sz, vp, sz, vp]
+        L.numarck_deflate_index.restype = i32
+        L.numarck_inflate_index.argtypes = [vp, sz, vp, vp, i64, i64, vp, vp]
+        L.numarck_inflate_index.restype = i32
         L.numarck_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(i32)]
         L.numarck_server_create.restype = vp
         L.numarck_server_submit.argtypes = [vp, ctypes.POINTER(Request),
@@ -366,6 +374,59 @@ def trace_events(events) -> None:
 
 def version() -> str:
     return lib().numarck_version().decode()
+
+
+ZINDEX_HEADER_BYTES = 64
+_ZINDEX_FMT = "<Iiiiqqqqqq"
+ZINDEX_FIELDS = ("magic", "version", "B", "pad", "n", "nblocks", "nsub", "off_zoff", "off_sub_zoff",
+                 "off_data")
+
+
+def deflate_index(blob: torch.Tensor, header: bytes, zindex: torch.Tensor | None = None,
+                  workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Lossless compression of the blob's index blocks into a container of zlib streams
+    (numarck_deflate_index); returns the container buffer (its size: zindex_size)."""
+    hp = ctypes.c_char_p(header)
+    if zindex is None:
+        zindex = torch.empty(lib().numarck_zindex_bound(hp), dtype=torch.uint8, device=blob.device)
+    if workspace is None:
+        workspace = torch.empty(lib().numarck_zindex_workspace_bytes(hp), dtype=torch.uint8,
+                                device=blob.device)
+    _check(lib().numarck_deflate_index(ctypes.c_void_p(blob.data_ptr()), hp,
+                                       ctypes.c_void_p(zindex.data_ptr()), zindex.numel(),
+                                       ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                       ctypes.c_void_p(_stream_ptr(stream))), "numarck_deflate_index")
+    return zindex
+
+
+def zindex_header(zindex: torch.Tensor) -> dict:
+    """The container header, with the container's size (zoff[nblocks]) as 'total_bytes'
+    (synchronises with the current stream)."""
+    raw = bytes(zindex[:ZINDEX_HEADER_BYTES].cpu().numpy().tobytes())
+    h = dict(zip(ZINDEX_FIELDS, struct.unpack(_ZINDEX_FMT, raw)))
+    at = h["off_zoff"] + 8 * h["nblocks"]
+    h["total_bytes"] = int(zindex[at:at + 8].cpu().view(torch.int64).item())
+    return h
+
+
+def zindex_offsets(zindex: torch.Tensor, h: dict):
+    """(zoff[nblocks + 1], sub_zoff[nsub]) as numpy arrays (host copies)."""
+    zo = zindex[h["off_zoff"]:h["off_zoff"] + 8 * (h["nblocks"] + 1)].cpu().view(torch.int64)
+    so = zindex[h["off_sub_zoff"]:h["off_sub_zoff"] + 8 * h["nsub"]].cpu().view(torch.int64)
+    return zo.numpy(), so.numpy()
+
+
+def inflate_index(zindex: torch.Tensor, zbytes: int, header: bytes, blob: torch.Tensor,
+                  start: int = 0, count: int | None = None, status: torch.Tensor | None = None,
+                  stream=None) -> None:
+    """Restores the index sub-blocks covering [start, start + count) into `blob`."""
+    n = parse_header(header)["n"]
+    cnt = n - start if count is None else count
+    sp = ctypes.c_void_p(status.data_ptr()) if status is not None else None
+    _check(lib().numarck_inflate_index(ctypes.c_void_p(zindex.data_ptr()), int(zbytes),
+                                       ctypes.c_char_p(header), ctypes.c_void_p(blob.data_ptr()),
+                                       int(start), int(cnt), sp,
+                                       ctypes.c_void_p(_stream_ptr(stream))), "numarck_inflate_index")
 
 
 class Server:
