@@ -57,7 +57,8 @@ def parse():
                     help="choose B per pair from the histogram (Eqs. 5-6) instead of B = 8, 10")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
-    ap.add_argument("--workload", default="flash", choices=["flash", "batched", "served"],
+    ap.add_argument("--workload", default="flash",
+                    choices=["flash", "batched", "served", "zindex"],
                     help="flash: the headline 1024^3 series; batched: 256 mixed variables, "
                          "per-variable launches vs one graph-captured batch")
     ap.add_argument("--batch-count", type=int, default=256)
@@ -312,6 +313,78 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_zindex(args):
+    """Lossless index compression (§IV.C) on the FLASH-like pair (timesteps 1 -> 2) at each
+    (E, B): deflate throughput (raw index bytes / time) and ratio, full inflate, and a partial
+    decompression of 1% of the points (inflate its sub-blocks + range decode) against the whole
+    decompression."""
+    import torch
+    from paper_1703_02438_gb300 import build as nbuild
+    from paper_1703_02438_gb300 import numarck as N
+    from paper_1703_02438_gb300 import synth
+    nbuild.build()
+    dev = torch.device("cuda", 0)
+    side = args.side
+    n = side ** 3
+    xs = synth.flash_series(side=side, steps=3, device=dev, seed=synth.seed_for(1, 0))
+    p, x = xs[1], xs[2]
+    del xs
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps=5, warm=2):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    rows = []
+    rng = np.random.default_rng(7)
+    for E, B in ((1e-3, 8), (1e-4, 10)):
+        blob = N.compress(p, x, E, B)
+        hb = N.header_bytes(blob)
+        h = N.parse_header(hb)
+        raw = sum(((min(n, (q + 1) * h["epb"]) - q * h["epb"]) * B + 7) // 8
+                  for q in range(h["nblocks"]))
+        zbuf = torch.empty(N.lib().numarck_zindex_bound(hb), dtype=torch.uint8, device=dev)
+        zws = torch.empty(N.lib().numarck_zindex_workspace_bytes(hb), dtype=torch.uint8, device=dev)
+        t_def = timed(lambda: N.deflate_index(blob, hb, zindex=zbuf, workspace=zws))
+        zh = N.zindex_header(zbuf)
+        zb = zh["total_bytes"]
+        copy = blob.clone()
+        t_inf = timed(lambda: N.inflate_index(zbuf, zb, hb, copy))
+        out = torch.empty_like(p)
+        t_full = timed(lambda: N.decompress(blob, p, header=hb, out=out))
+        cnt = n // 100
+        start = int(rng.integers(0, n - cnt))
+        seg = torch.empty(cnt, dtype=torch.float64, device=dev)
+
+        def partial():
+            N.inflate_index(zbuf, zb, hb, copy, start=start, count=cnt)
+            N.decompress_range(copy, p[start: start + cnt], start, cnt, header=hb, out=seg)
+        t_part = timed(partial)
+        rows.append({"E": E, "B": B, "index_bytes": raw, "zindex_bytes": zb,
+                     "index_ratio": raw / zb, "deflate_ms": t_def,
+                     "deflate_gbs": raw / (t_def / 1e3) / 1e9, "inflate_all_ms": t_inf,
+                     "inflate_gbs": raw / (t_inf / 1e3) / 1e9,
+                     "decompress_all_ms": t_full, "partial_1pct_ms": t_part,
+                     "blob_bytes": N.blob_size(hb),
+                     "blob_ratio_raw": n * 8 / N.blob_size(hb),
+                     "blob_ratio_deflated": n * 8 / (N.blob_size(hb)
+                                                     - (h["off_exact"] - h["off_index"]) + zb)})
+    line = {"metric": "lossless index compression (zlib streams): deflate/inflate GB/s, ratio, "
+                      "partial decode", "value": rows[0]["deflate_gbs"], "unit": "GB/s",
+            "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": f"FLASH-like float64 {side}^3 pair, E/B in (1e-3, 8), (1e-4, 10)"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_served(args):
     """The served form: 32 series (sizes log-uniform in [1 MB, 2 GB] of float32/float64 data,
     50/50), Poisson arrivals at --serve-rate requests/s for --serve-seconds; 80% compressions of
@@ -425,7 +498,7 @@ def run_served(args):
     print(json.dumps(line), flush=True)
 
 
-def run_e2e(args, xs, n, bound, dist, dev, ws):
+def run_e2e(args, xs, n, bound, dist, dev, ws, recon_out=True):
     """End-to-end metric through the public API: host timesteps in, blobs and reconstructions
     out, with host<->device copies overlapped with the kernels (see the comment in main)."""
     import torch
@@ -433,7 +506,10 @@ def run_e2e(args, xs, n, bound, dist, dev, ws):
     nC = len(COMBOS)
     host_x = [xs[t].cpu().pin_memory() for t in range(4)]
     host_blob = [torch.empty(bound, dtype=torch.uint8).pin_memory() for _ in range(2)]
-    host_rec = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(2)]
+    host_rec = [torch.empty(n if recon_out else 1, dtype=torch.float64).pin_memory()
+                for _ in range(2)]
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    host_status = torch.zeros(1, dtype=torch.int32).pin_memory()
     hdrs = [torch.empty(N.HEADER_BYTES, dtype=torch.uint8).pin_memory() for _ in range(2)]
     xin = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(3)]
     recs = [[torch.empty(n, dtype=torch.float64, device=dev) for _ in range(2)] for _ in range(nC)]
@@ -481,12 +557,16 @@ def run_e2e(args, xs, n, bound, dist, dev, ws):
             d2h.wait_event(ev_c)
             split_copy(host_blob[bi][:size], blobs[bi][:size], d2h, d2h_s)
             d2h.wait_event(ev_d)
-            split_copy(host_rec[k % 2], recs[c][ri], d2h, d2h_s)
+            if recon_out:
+                split_copy(host_rec[k % 2], recs[c][ri], d2h, d2h_s)
+            else:                                     # the decode status word only
+                with torch.cuda.stream(d2h):
+                    host_status.copy_(status, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(d2h)
             blob_free[bi] = ev
             rec_free[(c, ri)] = ev
-            tally["d2h"] += size + n * 8
+            tally["d2h"] += size + (n * 8 if recon_out else 4)
 
         load(0)
         load(1)
@@ -508,7 +588,7 @@ def run_e2e(args, xs, n, bound, dist, dev, ws):
                 hdrs[bi].copy_(blobs[bi][:N.HEADER_BYTES], non_blocking=True)
                 ev_c = torch.cuda.Event()
                 ev_c.record(comp)
-                N.decompress(blobs[bi], prev, out=recs[c][ri], stream=comp)
+                N.decompress(blobs[bi], prev, out=recs[c][ri], status=status, stream=comp)
                 ev_d = torch.cuda.Event()
                 ev_d.record(comp)
                 if pending is not None:
@@ -540,9 +620,10 @@ def run_e2e(args, xs, n, bound, dist, dev, ws):
            "h2d_bytes_per_step": tally["h2d"] // args.e2e_steps,
            "d2h_bytes_per_step": tally["d2h"] // args.e2e_steps,
            "steps": args.e2e_steps,
-           "note": "each timestep copied in once per step; every pair's blob and reconstruction "
-                   "copied out; copies split over 4 streams each way and overlapped with the "
-                   "kernels"}
+           "note": ("each timestep copied in once per step; every pair's blob and "
+                    + ("reconstruction" if recon_out else "decode status word")
+                    + " copied out; copies split over 4 streams each way and overlapped with "
+                      "the kernels")}
     del host_x, host_blob, host_rec, xin, recs, blobs
     return out
 
@@ -553,6 +634,8 @@ def main():
         return run_reference(args)
     if args.workload == "served":
         return run_served(args)
+    if args.workload == "zindex":
+        return run_zindex(args)
     if args.workload == "batched":
         return run_batched(args)
     rank, world = _rank_world()
@@ -674,9 +757,12 @@ def main():
     # host->device once per step (pinned, on its own stream, one timestep ahead of the kernels);
     # every pair's blob (the used bytes, sized from its header) and reconstruction are copied
     # device->host on a third stream while the next pair computes
-    e2e = None
+    e2e = e2e_blob = None
     if not args.no_e2e and args.e2e_steps > 0:
         e2e = run_e2e(args, xs, n, bound, dist, dev, ws)
+        # the same without the reconstruction leaving the device (it is the next prev of the
+        # closed loop, Eq. 4): the blobs and the decode status are the step's results
+        e2e_blob = run_e2e(args, xs, n, bound, dist, dev, ws, recon_out=False)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -703,7 +789,7 @@ def main():
             "compress_one_pass_frac": one_pass / (t_comp / 1e3) / 1e9 / peak,
             "decompress_gbs": n * 8 / (avg["k4_decode"] / 1e3) / 1e9,
             "alpha_last": alpha, "B_last": Bl, "auto_b": bool(args.auto_b),
-            "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+            "clocks": clk, "e2e": e2e, "e2e_blobs_only": e2e_blob, "cpu_baseline": cpu,
             "gpu_launches": args.steps * n_pairs * (8 if args.auto_b else 7),
         }
         print(json.dumps(line), flush=True)

@@ -7,7 +7,8 @@
 //   0x78 0x01                                       zlib header (deflate, 32 KB window)
 //   for each 4096-element sub-block t of the block:
 //     one fixed-Huffman DEFLATE block (BFINAL 0) of t's bytes, then an empty stored block
-//     (BFINAL 0, BTYPE 00, LEN 0, NLEN 0xFFFF) that ends t's data on a byte boundary
+//     (BFINAL 0, BTYPE 00, LEN 0, NLEN 0xFFFF) that ends t's data on a byte boundary; or, when
+//     that would be larger than t's bytes, one stored block (BFINAL 0, BTYPE 00) holding them
 //   0x03 0x00                                       empty fixed-Huffman block with BFINAL 1
 //   Adler-32 of the block's bytes, big-endian
 // Matches never reach before the start of their sub-block, so every sub-block's data can be
@@ -109,6 +110,7 @@ struct ZArgs {
 struct ZTile {
   const unsigned char* src;
   int tb;                    // ceil(cnt * B / 8)
+  int padded;                // the raw image's bytes (a multiple of 16, zero after tb)
   bool first, last;          // first / last sub-block of its index block
   long long q, t;
 };
@@ -121,6 +123,7 @@ __device__ __forceinline__ ZTile ztile(const ZArgs& A, long long gt) {
   const long long bend = min((long long)g.n, (long long)((z.q + 1) * g.epb));
   const int cnt = (int)min((long long)SUB, bend - j0);
   z.tb = (cnt * g.B + 7) / 8;
+  z.padded = 16 * ((cnt * g.B + 127) / 128);
   z.src = A.blob + g.off_index + z.q * g.block_stride + z.t * (long long)(SUB / 8 * g.B);
   z.first = z.t == 0;
   z.last = j0 + cnt == bend;
@@ -166,12 +169,15 @@ __device__ __forceinline__ int period_of(int B) {
   return B / a;
 }
 
-// Bytes of a sub-block's slot: its DEFLATE data (3 header bits, codes, end-of-block, then the
-// empty stored block: 3 bits, padding, 4 bytes), plus the zlib header before the first
-// sub-block of a block and the final block and Adler-32 after the last.
-__device__ __forceinline__ long long slot_bytes(int code_bits, bool first, bool last) {
-  const int bits = 3 + code_bits + 7 + 3;
-  return (bits + 7) / 8 + 4 + (first ? 2 : 0) + (last ? 6 : 0);
+// Bytes of a sub-block's DEFLATE data: fixed Huffman (3 header bits, codes, end-of-block, then
+// the empty stored block: 3 bits, padding, 4 bytes) or stored (header byte, LEN, NLEN, bytes),
+// whichever is smaller (stored on ties: fixed_bytes <= stored_bytes selects fixed).
+__device__ __forceinline__ int fixed_bytes(int code_bits) { return (3 + code_bits + 7 + 3 + 7) / 8 + 4; }
+__device__ __forceinline__ int stored_bytes(int tb) { return 1 + 4 + tb; }
+// A slot adds the zlib header before the first sub-block of a block and the final block and
+// Adler-32 after the last.
+__device__ __forceinline__ long long slot_bytes(int data_bytes, bool first, bool last) {
+  return data_bytes + (first ? 2 : 0) + (last ? 6 : 0);
 }
 
 // Z1: per sub-block, the slot size and the Adler-32 partial sums.
@@ -183,7 +189,8 @@ __global__ void __launch_bounds__(ZT) z1_size(ZArgs A) {
   for (long long gt = (long long)blockIdx.x * ZW + warp; gt < A.g.nsub;
        gt += (long long)gridDim.x * ZW) {
     const ZTile z = ztile(A, gt);
-    for (int i = lane; i < z.tb; i += 32) s[i] = z.src[i];
+    for (int i = lane; i < z.padded / 16; i += 32)
+      reinterpret_cast<uint4*>(s)[i] = __ldg(reinterpret_cast<const uint4*>(z.src) + i);
     __syncwarp();
     const int per = (z.tb + 31) / 32;
     const int c0 = min(z.tb, lane * per), c1 = min(z.tb, c0 + per);
@@ -199,7 +206,7 @@ __global__ void __launch_bounds__(ZT) z1_size(ZArgs A) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
     if (lane == 0) {
-      A.tile_bytes[gt] = slot_bytes(bits, z.first, z.last);
+      A.tile_bytes[gt] = slot_bytes(min(fixed_bytes(bits), stored_bytes(z.tb)), z.first, z.last);
       A.adler_a[gt] = a % ADLER;
       A.adler_w[gt] = (unsigned)(w % ADLER);
     }
@@ -273,7 +280,8 @@ __global__ void __launch_bounds__(ZT) z3_write(ZArgs A) {
   for (long long gt = (long long)blockIdx.x * ZW + warp; gt < A.g.nsub;
        gt += (long long)gridDim.x * ZW) {
     const ZTile z = ztile(A, gt);
-    for (int i = lane; i < z.tb; i += 32) s[i] = z.src[i];
+    for (int i = lane; i < z.padded / 16; i += 32)
+      reinterpret_cast<uint4*>(s)[i] = __ldg(reinterpret_cast<const uint4*>(z.src) + i);
     for (int i = lane; i < Z_OUT_WORDS; i += 32) o[i] = 0u;
     __syncwarp();
     const int per = (z.tb + 31) / 32;
@@ -286,36 +294,49 @@ __global__ void __launch_bounds__(ZT) z3_write(ZArgs A) {
       if (lane >= d) incl += u;
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
-    BitWriter bw{o, 3 + incl - bits};
-    if (lane == 0) {
-      BitWriter hw{o, 0};
-      hw.put(2u, 3);                       // BFINAL 0, BTYPE 01 (fixed Huffman)
-    }
-    parse_chunk(s, c0, c1, p, &bw);
-    __syncwarp();
-    int end_bits = 3 + total;
-    if (lane == 0) {
-      BitWriter ew{o, end_bits};
-      ew.put(0u, 7);                       // end of block (symbol 256)
-      ew.put(0u, 3);                       // BFINAL 0, BTYPE 00 (stored), LEN 0 follows
-    }
-    __syncwarp();
-    end_bits += 10;
-    const int nb = (end_bits + 7) / 8;     // bytes of codes, padded to a byte boundary
     const long long off = A.tile_bytes[gt];
     unsigned char* dst = A.z + off;
-    int k = 0;
-    if (z.first) {
-      if (lane == 0) { dst[0] = 0x78; dst[1] = 0x01; }
-      k = 2;
+    const int k = z.first ? 2 : 0;
+    if (z.first && lane == 0) { dst[0] = 0x78; dst[1] = 0x01; }
+    int nb;                                // bytes of the sub-block's DEFLATE data
+    if (fixed_bytes(total) > stored_bytes(z.tb)) {
+      // stored block: BFINAL 0, BTYPE 00 (the rest of the header byte is padding), LEN, NLEN
+      if (lane == 0) {
+        dst[k] = 0x00;
+        dst[k + 1] = (unsigned char)z.tb; dst[k + 2] = (unsigned char)(z.tb >> 8);
+        dst[k + 3] = (unsigned char)~z.tb; dst[k + 4] = (unsigned char)(~z.tb >> 8);
+      }
+      for (int i = lane; i < z.tb; i += 32) dst[k + 5 + i] = s[i];
+      nb = stored_bytes(z.tb);
+    } else {
+      BitWriter bw{o, 3 + incl - bits};
+      if (lane == 0) {
+        BitWriter hw{o, 0};
+        hw.put(2u, 3);                       // BFINAL 0, BTYPE 01 (fixed Huffman)
+      }
+      parse_chunk(s, c0, c1, p, &bw);
+      __syncwarp();
+      int end_bits = 3 + total;
+      if (lane == 0) {
+        BitWriter ew{o, end_bits};
+        ew.put(0u, 7);                       // end of block (symbol 256)
+        ew.put(0u, 3);                       // BFINAL 0, BTYPE 00 (stored), LEN 0 follows
+      }
+      __syncwarp();
+      end_bits += 10;
+      const int cb = (end_bits + 7) / 8;     // bytes of codes, padded to a byte boundary
+      const unsigned char* ob = reinterpret_cast<const unsigned char*>(o);
+      for (int i = lane; i < cb; i += 32) dst[k + i] = ob[i];
+      if (lane == 0) {
+        unsigned char* tail = dst + k + cb;
+        tail[0] = 0x00; tail[1] = 0x00; tail[2] = 0xFF; tail[3] = 0xFF;   // LEN 0, NLEN 0xFFFF
+      }
+      nb = cb + 4;
     }
-    const unsigned char* ob = reinterpret_cast<const unsigned char*>(o);
-    for (int i = lane; i < nb; i += 32) dst[k + i] = ob[i];
     if (lane == 0) {
       unsigned char* tail = dst + k + nb;
-      tail[0] = 0x00; tail[1] = 0x00; tail[2] = 0xFF; tail[3] = 0xFF;   // LEN 0, NLEN 0xFFFF
       if (z.last) {
-        tail[4] = 0x03; tail[5] = 0x00;    // empty fixed-Huffman block with BFINAL 1
+        tail[0] = 0x03; tail[1] = 0x00;    // empty fixed-Huffman block with BFINAL 1
         // Adler-32 of the block: combine its sub-blocks' partial sums in order
         const long long g0 = z.q * A.g.spb;
         unsigned long long sa = 1, sb = 0;
@@ -330,8 +351,8 @@ __global__ void __launch_bounds__(ZT) z3_write(ZArgs A) {
         sb = (sb + (unsigned long long)(after % ADLER)) % ADLER;
         sa %= ADLER;
         const unsigned ad = (unsigned)((sb << 16) | sa);
-        tail[6] = (unsigned char)(ad >> 24); tail[7] = (unsigned char)(ad >> 16);
-        tail[8] = (unsigned char)(ad >> 8);  tail[9] = (unsigned char)ad;
+        tail[2] = (unsigned char)(ad >> 24); tail[3] = (unsigned char)(ad >> 16);
+        tail[4] = (unsigned char)(ad >> 8);  tail[5] = (unsigned char)ad;
       }
     }
     __syncwarp();
@@ -349,38 +370,87 @@ struct InflateArgs {
   long long zbytes;
 };
 
-struct BitReader {
-  const unsigned char* p;
-  long long pos, end;       // bit position, end (bits)
-  __device__ __forceinline__ unsigned peek(int n) const {   // n <= 24
-    const long long byte = pos >> 3;
-    unsigned v = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if ((byte + k) * 8 < end) v |= (unsigned)p[byte + k] << (8 * k);
-    return (v >> (pos & 7)) & ((1u << n) - 1u);
+constexpr int ZI_T = 128;                         // inflate: threads per CTA (one sub-block each)
+
+// Bits of the container from byte `from` on, LSB first, through a 64-bit reservoir refilled
+// with aligned 32-bit loads (the last partial word byte by byte); past `end` it reads zeros.
+struct RegBits {
+  const unsigned char* z;
+  long long word;             // next word to load (index of 4-byte words)
+  long long end;              // bytes of the container
+  unsigned long long buf;
+  int nbits;
+  long long used;             // bits consumed
+  __device__ __forceinline__ void init(const unsigned char* zz, long long from, long long e) {
+    z = zz;
+    end = e;
+    word = from >> 2;
+    buf = 0;
+    nbits = 0;
+    used = 0;
+    refill();
+    const int skip = (int)(from & 3) * 8;
+    buf >>= skip;
+    nbits -= skip;
+  }
+  __device__ __forceinline__ void refill() {
+    while (nbits <= 32) {
+      unsigned v = 0;
+      const long long at = word * 4;
+      if (at + 4 <= end) {
+        v = __ldg(reinterpret_cast<const unsigned*>(z) + word);
+      } else {
+        for (int k = 0; k < 4; ++k)
+          if (at + k < end) v |= (unsigned)z[at + k] << (8 * k);
+      }
+      buf |= (unsigned long long)v << nbits;
+      nbits += 32;
+      ++word;
+    }
+  }
+  __device__ __forceinline__ unsigned peek(int n) { return (unsigned)buf & ((1u << n) - 1u); }
+  __device__ __forceinline__ void skip(int n) {
+    buf >>= n;
+    nbits -= n;
+    used += n;
+    refill();
   }
   __device__ __forceinline__ unsigned get(int n) {
     const unsigned v = n ? peek(n) : 0u;
-    pos += n;
+    skip(n);
     return v;
   }
 };
 
-// Decodes one fixed-Huffman literal/length symbol; -1 if invalid.
-__device__ __forceinline__ int fixed_symbol(BitReader& br) {
-  const unsigned c7 = rev(br.peek(7), 7);
-  if (c7 <= 23) { br.pos += 7; return 256 + (int)c7; }
-  const unsigned c8 = rev(br.peek(8), 8);
-  if (c8 >= 0x30 && c8 <= 0xBF) { br.pos += 8; return (int)(c8 - 0x30); }
-  if (c8 >= 0xC0 && c8 <= 0xC7) { br.pos += 8; return 280 + (int)(c8 - 0xC0); }
-  const unsigned c9 = rev(br.peek(9), 9);
-  if (c9 >= 0x190) { br.pos += 9; return 144 + (int)(c9 - 0x190); }
-  return -1;
-}
+// Decoded bytes go out as 32-bit words (the raw image starts on a 16-byte boundary); the last
+// 16 bytes are kept in registers for matches (this encoder's distances are at most 15).
+struct ByteOut {
+  unsigned* dst;
+  int n;                      // bytes written
+  unsigned acc;
+  unsigned long long h0, h1;  // h0: the 8 most recent bytes (byte 0 = last), h1: the 8 before
+  __device__ __forceinline__ void put(unsigned b) {
+    acc |= b << (8 * (n & 3));
+    h1 = (h1 << 8) | (h0 >> 56);
+    h0 = (h0 << 8) | b;
+    ++n;
+    if ((n & 3) == 0) { dst[(n >> 2) - 1] = acc; acc = 0; }
+  }
+  __device__ __forceinline__ unsigned back(int d) const {   // the byte d back (1 <= d <= 16)
+    return d <= 8 ? (unsigned)(h0 >> (8 * (d - 1))) & 0xFFu : (unsigned)(h1 >> (8 * (d - 9))) & 0xFFu;
+  }
+};
 
-__global__ void __launch_bounds__(128) z4_inflate(InflateArgs A, const int64_t* sub_zoff) {
-  const long long gt = A.g0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// One thread per sub-block (LPT = 1) or one warp per sub-block with only its first lane
+// decoding (LPT = 32: no divergence between sub-blocks, for small counts where latency rather
+// than throughput matters): inflates the sub-block's DEFLATE data (the fixed-Huffman and stored
+// blocks this encoder writes; anything else is NUMARCK_ERR_CORRUPT) into the raw image and
+// pads it.
+template <int LPT>
+__global__ void __launch_bounds__(ZI_T) z4_inflate(InflateArgs A, const int64_t* sub_zoff) {
+  const long long tid = (long long)blockIdx.x * ZI_T + threadIdx.x;
+  if (tid % LPT) return;
+  const long long gt = A.g0 + tid / LPT;
   if (gt > A.g1) return;
   const Geometry& g = A.g;
   const long long q = gt / g.spb, t = gt - q * g.spb;
@@ -392,18 +462,42 @@ __global__ void __launch_bounds__(128) z4_inflate(InflateArgs A, const int64_t* 
   unsigned char* dst = A.blob + g.off_index + q * g.block_stride + t * (long long)(SUB / 8 * g.B);
   const long long zo = sub_zoff[gt];
   const long long zend = gt + 1 < g.nsub ? sub_zoff[gt + 1] : A.zbytes;
-  int rc = 0;
-  if (zo < 0 || zo > zend || zend > A.zbytes) rc = NUMARCK_ERR_CORRUPT;
-  BitReader br{A.z + (rc ? 0 : zo), 0, rc ? 0 : (zend - zo) * 8};
-  int n = 0;
-  if (!rc && br.get(3) != 2u) rc = NUMARCK_ERR_CORRUPT;   // BFINAL 0, BTYPE 01
-  while (!rc) {
-    if (br.pos > br.end) { rc = NUMARCK_ERR_CORRUPT; break; }
-    const int sym = fixed_symbol(br);
-    if (sym < 0 || sym > 285) { rc = NUMARCK_ERR_CORRUPT; break; }
+  int rc = (zo < 0 || zo > zend || zend > A.zbytes) ? NUMARCK_ERR_CORRUPT : 0;
+  RegBits br;
+  br.init(A.z, rc ? 0 : zo, rc ? 0 : zend);
+  const long long limit = rc ? 0 : (zend - zo) * 8;
+  ByteOut out{reinterpret_cast<unsigned*>(dst), 0, 0u, 0ull, 0ull};
+  const unsigned hdr = rc ? 0u : br.get(3);
+  if (!rc && hdr == 0u) {                         // stored: BFINAL 0, BTYPE 00
+    br.skip((8 - (int)(br.used & 7)) & 7);        // to the byte boundary
+    const unsigned len = br.get(16), nlen = br.get(16);
+    if ((len ^ nlen) != 0xFFFFu || (int)len != tb || br.used + 8LL * len > limit) {
+      rc = NUMARCK_ERR_CORRUPT;
+    } else {
+      for (int k = 0; k < tb; ++k) out.put(br.get(8));
+    }
+  } else if (!rc && hdr != 2u) {                  // neither stored nor BTYPE 01
+    rc = NUMARCK_ERR_CORRUPT;
+  }
+  while (!rc && hdr == 2u) {
+    if (br.used > limit) { rc = NUMARCK_ERR_CORRUPT; break; }
+    // fixed Huffman literal/length symbol (RFC 1951 §3.2.6)
+    const unsigned b9 = br.peek(9);
+    int sym;
+    const unsigned c7 = rev(b9 & 0x7Fu, 7);
+    if (c7 <= 23) {
+      sym = 256 + (int)c7;
+      br.skip(7);
+    } else {
+      const unsigned c8 = rev(b9 & 0xFFu, 8);
+      if (c8 >= 0x30 && c8 <= 0xBF) { sym = (int)(c8 - 0x30); br.skip(8); }
+      else if (c8 >= 0xC0 && c8 <= 0xC7) { sym = 280 + (int)(c8 - 0xC0); br.skip(8); }
+      else { sym = 144 + (int)(rev(b9, 9) - 0x190); br.skip(9); }
+    }
+    if (sym > 285) { rc = NUMARCK_ERR_CORRUPT; break; }
     if (sym < 256) {
-      if (n >= tb) { rc = NUMARCK_ERR_CORRUPT; break; }
-      dst[n++] = (unsigned char)sym;
+      if (out.n >= tb) { rc = NUMARCK_ERR_CORRUPT; break; }
+      out.put((unsigned)sym);
     } else if (sym == 256) {
       break;
     } else {
@@ -412,13 +506,27 @@ __global__ void __launch_bounds__(128) z4_inflate(InflateArgs A, const int64_t* 
       const int dc = (int)rev(br.get(5), 5);
       if (dc > 29) { rc = NUMARCK_ERR_CORRUPT; break; }
       const int d = c_dist_base[dc] + (int)br.get(c_dist_extra[dc]);
-      if (d > n || n + len > tb) { rc = NUMARCK_ERR_CORRUPT; break; }
-      for (int k = 0; k < len; ++k, ++n) dst[n] = dst[n - d];
+      if (d > out.n || out.n + len > tb) { rc = NUMARCK_ERR_CORRUPT; break; }
+      if (d <= 16) {
+        for (int k = 0; k < len; ++k) out.put(out.back(d));
+      } else {                                    // not written by this encoder: from memory
+        for (int k = 0; k < len; ++k) {
+          const int at = out.n - d;
+          const unsigned b = (at >> 2) < (out.n >> 2)
+                                 ? (reinterpret_cast<const unsigned*>(dst)[at >> 2] >> (8 * (at & 3))) & 0xFFu
+                                 : (out.acc >> (8 * (at & 3))) & 0xFFu;
+          out.put(b);
+        }
+      }
     }
   }
-  if (!rc && n != tb) rc = NUMARCK_ERR_CORRUPT;
-  for (int k = tb; k < padded; ++k) dst[k] = 0;       // the raw blob pads images to 16 bytes
-  if (rc && A.status) atomicExch(A.status, rc);
+  if (!rc && out.n != tb) rc = NUMARCK_ERR_CORRUPT;
+  if (rc) {
+    if (A.status) atomicExch(A.status, rc);
+    return;
+  }
+  if (out.n & 3) out.dst[out.n >> 2] = out.acc;   // the last partial word (zero-padded)
+  for (int w = (tb + 3) >> 2; w < padded / 4; ++w) out.dst[w] = 0u;
 }
 
 }  // namespace
@@ -457,7 +565,7 @@ cudaError_t launch_deflate(const unsigned char* blob, const Geometry& g, unsigne
   A.adler_a = reinterpret_cast<unsigned*>(ws + g.nsub * 8);
   A.adler_w = A.adler_a + g.nsub;
   long long blocks = (g.nsub + ZW - 1) / ZW;
-  if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
+  if (blocks > (long long)sms * 32) blocks = (long long)sms * 32;
   z1_size<<<(int)blocks, ZT, 0, s>>>(A);
   z2_scan<<<1, 1024, 0, s>>>(A);
   z3_write<<<(int)blocks, ZT, 0, s>>>(A);
@@ -474,7 +582,10 @@ cudaError_t launch_inflate(const unsigned char* z, long long zbytes, unsigned ch
   numarck_zindex_header lay;
   zindex_layout(g, &lay);
   const int64_t* sub_zoff = reinterpret_cast<const int64_t*>(z + lay.off_sub_zoff);
-  z4_inflate<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(A, sub_zoff);
+  if (n < 16384)     // few sub-blocks (a partial decompression): one warp each, all SMs busy
+    z4_inflate<32><<<(unsigned)((n * 32 + ZI_T - 1) / ZI_T), ZI_T, 0, s>>>(A, sub_zoff);
+  else
+    z4_inflate<1><<<(unsigned)((n + ZI_T - 1) / ZI_T), ZI_T, 0, s>>>(A, sub_zoff);
   return cudaGetLastError();
 }
 
