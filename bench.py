@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 24,
                     help="elements of the oracle's bounded sample")
+    ap.add_argument("--f32", action="store_true",
+                    help="the same series as float32 (4 bytes per element)")
     ap.add_argument("--auto-b", action="store_true",
                     help="choose B per pair from the histogram (Eqs. 5-6) instead of B = 8, 10")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
@@ -504,15 +506,17 @@ def run_e2e(args, xs, n, bound, dist, dev, ws, recon_out=True):
     import torch
     from paper_1703_02438_gb300 import numarck as N
     nC = len(COMBOS)
+    tdt = xs[0].dtype
+    L = xs[0].element_size()
     host_x = [xs[t].cpu().pin_memory() for t in range(4)]
     host_blob = [torch.empty(bound, dtype=torch.uint8).pin_memory() for _ in range(2)]
-    host_rec = [torch.empty(n if recon_out else 1, dtype=torch.float64).pin_memory()
+    host_rec = [torch.empty(n if recon_out else 1, dtype=tdt).pin_memory()
                 for _ in range(2)]
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     host_status = torch.zeros(1, dtype=torch.int32).pin_memory()
     hdrs = [torch.empty(N.HEADER_BYTES, dtype=torch.uint8).pin_memory() for _ in range(2)]
-    xin = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(3)]
-    recs = [[torch.empty(n, dtype=torch.float64, device=dev) for _ in range(2)] for _ in range(nC)]
+    xin = [torch.empty(n, dtype=tdt, device=dev) for _ in range(3)]
+    recs = [[torch.empty(n, dtype=tdt, device=dev) for _ in range(2)] for _ in range(nC)]
     blobs = [torch.empty(bound, dtype=torch.uint8, device=dev) for _ in range(2)]
     comp = torch.cuda.current_stream()
     h2d = torch.cuda.Stream()
@@ -548,7 +552,7 @@ def run_e2e(args, xs, n, bound, dist, dev, ws, recon_out=True):
             ev = torch.cuda.Event()
             ev.record(h2d)
             loaded[t] = ev
-            tally["h2d"] += n * 8
+            tally["h2d"] += n * L
 
         def flush(pend):
             k, bi, ev_c, ev_d, c, ri = pend
@@ -566,7 +570,7 @@ def run_e2e(args, xs, n, bound, dist, dev, ws, recon_out=True):
             ev.record(d2h)
             blob_free[bi] = ev
             rec_free[(c, ri)] = ev
-            tally["d2h"] += size + (n * 8 if recon_out else 4)
+            tally["d2h"] += size + (n * L if recon_out else 4)
 
         load(0)
         load(1)
@@ -615,7 +619,7 @@ def run_e2e(args, xs, n, bound, dist, dev, ws, recon_out=True):
     torch.cuda.synchronize()
     e2e_ms = _max_over_ranks(dist, a.elapsed_time(b))
     n_pairs = 3 * nC
-    val = _sum_over_ranks(dist, args.e2e_steps * n_pairs * n * 8) / (e2e_ms / 1e3) / 1e9
+    val = _sum_over_ranks(dist, args.e2e_steps * n_pairs * n * L) / (e2e_ms / 1e3) / 1e9
     out = {"value": val, "unit": "GB/s",
            "h2d_bytes_per_step": tally["h2d"] // args.e2e_steps,
            "d2h_bytes_per_step": tally["d2h"] // args.e2e_steps,
@@ -657,12 +661,16 @@ def main():
     side = args.side
     n = side ** 3
     xs = synth.flash_series(side=side, steps=4, device=dev, seed=synth.seed_for(1, rank))
+    tdt = torch.float32 if args.f32 else torch.float64
+    L = 4 if args.f32 else 8
+    if args.f32:
+        xs = [x.float() for x in xs]
     torch.cuda.synchronize()
     combos = [(E, 0 if args.auto_b else B) for E, B in COMBOS]
-    params = {(E, B): N.make_params(torch.float64, B, E) for E, B in combos}
+    params = {(E, B): N.make_params(tdt, B, E) for E, B in combos}
     bound = max(N.compress_bound(n, p) for p in params.values())
     blob = torch.empty(bound, dtype=torch.uint8, device=dev)
-    recon = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(2)]
+    recon = [torch.empty(n, dtype=tdt, device=dev) for _ in range(2)]
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     ws = N.Workspace(dev)
     ws.get(max(N.workspace_bytes(n, p) for p in params.values()))
@@ -715,7 +723,7 @@ def main():
     ms_total = t_start.elapsed_time(t_end)
     ms_total = _max_over_ranks(dist, ms_total)
     ms_step = ms_total / args.steps
-    bytes_rank = args.steps * n_pairs * n * 8
+    bytes_rank = args.steps * n_pairs * n * L
     value = _sum_over_ranks(dist, bytes_rank) / (ms_total / 1e3) / 1e9
 
     # per-kernel times from the trace events: compress K1, K2, K3a, K3b, K3c; decompress K4
@@ -740,10 +748,10 @@ def main():
     # packed indices and 1 bit per point of incompressible flags; K3c reads the flags, gathers
     # the incompressible values of cur and writes them; K4 reads p (compressible points), the
     # packed indices and the incompressible values and writes R.
-    alg = {"k1_hist": 2 * 8 * n + 2 * n,
+    alg = {"k1_hist": 2 * L * n + 2 * n,
            "k3_assign": 2 * n + n * Bl / 8 + n / 8,
-           "k3_exact": n / 8 + 2 * alpha * n * 8,
-           "k4_decode": (1 - alpha) * n * 8 + n * Bl / 8 + alpha * n * 8 + n * 8}
+           "k3_exact": n / 8 + 2 * alpha * n * L,
+           "k4_decode": (1 - alpha) * n * L + n * Bl / 8 + alpha * n * L + n * L}
     dominant = max(alg, key=lambda k: avg[k])
     peak, peak_kind = _peaks()
     achieved = alg[dominant] / (avg[dominant] / 1e3) / 1e9
@@ -751,7 +759,7 @@ def main():
     kernel_gbs = {k: round(alg[k] / (avg[k] / 1e3) / 1e9, 1) for k in alg}
     t_comp = sum(avg[k] for k in ("k1_hist", "k2_topk", "k3_assign", "k3_scan", "k3_exact"))
     comp_alg = alg["k1_hist"] + alg["k3_assign"] + alg["k3_exact"]
-    one_pass = 2 * 8 * n + n * Bl / 8 + alpha * n * 8      # read p, x once; write the blob once
+    one_pass = 2 * L * n + n * Bl / 8 + alpha * n * L      # read p, x once; write the blob once
 
     # end to end through the public API with host buffers, pipelined: each timestep is copied
     # host->device once per step (pinned, on its own stream, one timestep ahead of the kernels);
@@ -774,9 +782,12 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.f32 else "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "pairs_per_step": n_pairs,
+            "config": {"workload": (WORKLOAD.replace("float64", "float32 (cast)").replace(
+                           "8 GiB/step", "4 GiB/step") if args.f32 else WORKLOAD),
+                       "n": n, "pairs_per_step": n_pairs,
                        "l2": "inputs 8 GiB per array >> 129 MB L2: no flush",
                        "parallelism": f"replicas x{world} (independent series per GPU)"},
             "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved,
@@ -784,10 +795,10 @@ def main():
                          "frac": achieved / peak, "traffic": _traffic(dominant, side),
                          "algorithmic_bytes_per_launch": alg[dominant]},
             "kernels_ms": kernel_ms, "kernels_gbs": kernel_gbs,
-            "compress_gbs": n * 8 / (t_comp / 1e3) / 1e9,
+            "compress_gbs": n * L / (t_comp / 1e3) / 1e9,
             "compress_path_hbm_frac": comp_alg / (t_comp / 1e3) / 1e9 / peak,
             "compress_one_pass_frac": one_pass / (t_comp / 1e3) / 1e9 / peak,
-            "decompress_gbs": n * 8 / (avg["k4_decode"] / 1e3) / 1e9,
+            "decompress_gbs": n * L / (avg["k4_decode"] / 1e3) / 1e9,
             "alpha_last": alpha, "B_last": Bl, "auto_b": bool(args.auto_b),
             "clocks": clk, "e2e": e2e, "e2e_blobs_only": e2e_blob, "cpu_baseline": cpu,
             "gpu_launches": args.steps * n_pairs * (8 if args.auto_b else 7),

@@ -248,21 +248,51 @@ __global__ void __launch_bounds__(K3_THREADS, 1) k3_assign(AssignArgs<T> A) {
     const TileRef tr = tile_ref<B>(g, gt, A.blob, A.codes);
     const int cnt = tr.cnt;
     const unsigned short* ct = A.codes + tr.j0;
-    const bool al = (tr.j0 & 3) == 0;           // codes of the tile 8-byte aligned
+    // codes are read as 8-byte words aligned in the codes array: a tile that starts sh codes
+    // past such a word takes each lane's four codes from its word and the next lane's
+    const int sh = (int)(tr.j0 & 3);
+    const long long wbase = tr.j0 - sh;          // first aligned word of the tile (in codes)
+    const unsigned short* cw = A.codes + wbase;
     int count = 0;
     unsigned far = 0;                            // > M (B < 16) or non-zero: CODE_FAR seen
     for (int s0 = 0; s0 < cnt; s0 += K3_SEG * K3_UNROLL) {
       uint2 cd[K3_UNROLL];   // four 16-bit codes per lane and step
+      if (sh == 0) {                             // uniform across the warp
 #pragma unroll
-      for (int u = 0; u < K3_UNROLL; ++u) {
-        const int e0 = s0 + u * K3_SEG + lane * 4;
-        if (al && e0 + 4 <= cnt) {
-          cd[u] = __ldcs(reinterpret_cast<const uint2*>(ct + e0));
-        } else {
-          unsigned v[4];
+        for (int u = 0; u < K3_UNROLL; ++u) {
+          const int e0 = s0 + u * K3_SEG + lane * 4;
+          if (e0 + 4 <= cnt) {
+            cd[u] = __ldcs(reinterpret_cast<const uint2*>(ct + e0));
+          } else {
+            unsigned v[4];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) v[k] = e0 + k < cnt ? (unsigned)ct[e0 + k] : CODE_NONE;
-          cd[u] = make_uint2(v[0] | (v[1] << 16), v[2] | (v[3] << 16));
+            for (int k = 0; k < 4; ++k) v[k] = e0 + k < cnt ? (unsigned)ct[e0 + k] : CODE_NONE;
+            cd[u] = make_uint2(v[0] | (v[1] << 16), v[2] | (v[3] << 16));
+          }
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < K3_UNROLL; ++u) {
+          const int e0 = s0 + u * K3_SEG + lane * 4;
+          const long long w0 = wbase + e0;       // this lane's aligned word (in codes)
+          const uint2 lo = w0 + 4 <= g.n ? __ldcs(reinterpret_cast<const uint2*>(cw + e0))
+                                         : make_uint2(0u, 0u);
+          uint2 hi;
+          hi.x = __shfl_down_sync(0xffffffffu, lo.x, 1);
+          hi.y = __shfl_down_sync(0xffffffffu, lo.y, 1);
+          const bool vec = e0 + 4 <= cnt && w0 + 8 <= g.n;   // both words in the codes array
+          if (lane == 31 && vec) hi = __ldcs(reinterpret_cast<const uint2*>(cw + e0 + 4));
+          if (vec) {
+            const unsigned long long L = ((unsigned long long)lo.y << 32) | lo.x;
+            const unsigned long long H = ((unsigned long long)hi.y << 32) | hi.x;
+            const unsigned long long V = (L >> (16 * sh)) | (H << (64 - 16 * sh));
+            cd[u] = make_uint2((unsigned)V, (unsigned)(V >> 32));
+          } else {
+            unsigned v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] = e0 + k < cnt ? (unsigned)ct[e0 + k] : CODE_NONE;
+            cd[u] = make_uint2(v[0] | (v[1] << 16), v[2] | (v[3] << 16));
+          }
         }
       }
 #pragma unroll

@@ -67,7 +67,10 @@ __device__ __forceinline__ void st4(float* p, const float* v) {
 constexpr int K4_WARPS = 16;                    // warps per CTA (each owns whole tiles)
 constexpr int K4_THREADS = K4_WARPS * 32;
 constexpr int K4_SEG = 128;                     // elements per warp step: 4 consecutive per lane
-constexpr int K4_UNROLL = 1;                    // steps whose loads are in flight together
+// steps whose loads are in flight together: float32 moves half the bytes per load, so it
+// keeps two steps in flight to have as many bytes outstanding as float64 with one
+template <typename T>
+__host__ __device__ constexpr int k4_unroll() { return sizeof(T) == 4 ? 2 : 1; }
 
 template <int B>
 struct Field {
@@ -148,11 +151,11 @@ __device__ __forceinline__ void decode_tiles(const DecodeArgs& A, const Geometry
     const bool vec = e_lo == 0 && ((reinterpret_cast<uintptr_t>(pt) |
                                     reinterpret_cast<uintptr_t>(ot)) & 15) == 0;
     long long run = base;
-    for (int s0 = 0; s0 < e_hi; s0 += K4_SEG * K4_UNROLL) {
-      F field[K4_UNROLL];
-      T pv[K4_UNROLL][4];
+    for (int s0 = 0; s0 < e_hi; s0 += K4_SEG * k4_unroll<T>()) {
+      F field[k4_unroll<T>()];
+      T pv[k4_unroll<T>()][4];
 #pragma unroll
-      for (int u = 0; u < K4_UNROLL; ++u) {
+      for (int u = 0; u < k4_unroll<T>(); ++u) {
         const int sb0 = s0 + u * K4_SEG;
         const int e0 = sb0 + 4 * lane;
         field[u] = sb0 < e_hi ? load_field<B>(tw, twords, (sb0 / K4_SEG) * FB, lane) : (F)0;
@@ -165,7 +168,7 @@ __device__ __forceinline__ void decode_tiles(const DecodeArgs& A, const Geometry
         }
       }
 #pragma unroll
-      for (int u = 0; u < K4_UNROLL; ++u) {
+      for (int u = 0; u < k4_unroll<T>(); ++u) {
         const int sb0 = s0 + u * K4_SEG;
         if (sb0 >= e_hi) break;                  // uniform across the warp
         const int e0 = sb0 + 4 * lane;
