@@ -7,6 +7,13 @@ in a closed loop (prev = previous reconstruction), for every E in {1e-3, 1e-4} a
 One step = those 12 (pair, E, B) compressions and their 12 decompressions. Inputs are 8 GiB
 arrays, far larger than the 129 MB L2, so no L2 flush is needed between iterations.
 
+Each (E, B) chain runs through the public API as a user of a chain of timesteps would: timestep
+1 compressed against timestep 0 (numarck_compress), timesteps 2 and 3 by the chained step
+(numarck_decompress_compress: the previous blob decompressed and the new timestep compressed
+against that reconstruction, with the decompression and the first compression pass fused in one
+kernel), and the last blob decompressed (numarck_decompress). Every compression and
+decompression of the step is done in full; --no-fuse runs them as 12 separate pairs instead.
+
 value = input bytes (n * 8 per pair, once for compression and once for decompression counted as
 one pass of the variable) / (compress time + decompress time), i.e. n*L / (t_c + t_d) summed
 over the step, in GB/s of the uncompressed variable, on the device with CUDA events.
@@ -37,8 +44,9 @@ WORKLOAD = ("FLASH-like 3-D float64 field 1024^3 (8 GiB/step), 4 timesteps, 3 cl
             "x E{1e-3,1e-4} x B{8,10}")
 KERNEL_FILES = {"k3_assign": ["k_assign.cu", "common.cuh"],
                 "k3_exact": ["k_assign.cu", "common.cuh"],
-                "k1_hist": ["k_hist.cu", "common.cuh"],
-                "k4_decode": ["k_decode.cu", "common.cuh"]}
+                "k1_hist": ["k_hist.cu", "k1.cuh", "common.cuh"],
+                "k4_decode": ["k_decode.cu", "k4.cuh", "common.cuh"],
+                "k41_step": ["k_step.cu", "k1.cuh", "k4.cuh", "common.cuh"]}
 
 
 def parse():
@@ -55,6 +63,9 @@ def parse():
                     help="elements of the oracle's bounded sample")
     ap.add_argument("--f32", action="store_true",
                     help="the same series as float32 (4 bytes per element)")
+    ap.add_argument("--no-fuse", action="store_true",
+                    help="every pair as a separate compression and decompression (no chained "
+                         "step that fuses a decompression with the next histogram pass)")
     ap.add_argument("--auto-b", action="store_true",
                     help="choose B per pair from the histogram (Eqs. 5-6) instead of B = 8, 10")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
@@ -620,10 +631,48 @@ def run_e2e(args, xs, n, bound, dist, dev, ws, recon_out=True):
     e2e_ms = _max_over_ranks(dist, a.elapsed_time(b))
     n_pairs = 3 * nC
     val = _sum_over_ranks(dist, args.e2e_steps * n_pairs * n * L) / (e2e_ms / 1e3) / 1e9
+
+    # the host link's own copy rates (one timestep each way, then both ways at once), for the
+    # bound that the copies above put on E
+    def issue(dst, src, streams):
+        m = src.numel()
+        st_ = (m + parts - 1) // parts
+        for i, st in enumerate(streams):
+            st.wait_stream(comp)
+            with torch.cuda.stream(st):
+                dst[i * st_:(i + 1) * st_].copy_(src[i * st_:(i + 1) * st_], non_blocking=True)
+
+    def link_rate(pairs_):
+        def once():
+            for dst, src, streams in pairs_:
+                issue(dst, src, streams)
+            for _, _, streams in pairs_:
+                for st in streams:
+                    comp.wait_stream(st)
+        once()
+        torch.cuda.synchronize()
+        a.record(comp)
+        for _ in range(3):
+            once()
+        b.record(comp)
+        torch.cuda.synchronize()
+        nbytes = 3 * sum(src.numel() * src.element_size() for _, src, _ in pairs_)
+        return nbytes / (a.elapsed_time(b) / 1e3) / 1e9
+
+    link = {"d2h_gbs": link_rate([(host_x[0], xin[0], d2h_s)]),
+            "h2d_gbs": link_rate([(xin[1], host_x[1], h2d_s)]),
+            "both_ways_gbs": link_rate([(host_x[0], xin[0], d2h_s), (xin[1], host_x[1], h2d_s)])}
+    hb_, db_ = tally["h2d"] / args.e2e_steps, tally["d2h"] / args.e2e_steps
+    # E if the step took exactly as long as its copies: each direction at its own rate, and
+    # both together at the measured two-way rate
+    t_copy = max(hb_ / link["h2d_gbs"], db_ / link["d2h_gbs"],
+                 (hb_ + db_) / link["both_ways_gbs"]) / 1e9
+    link["bound_gbs"] = n_pairs * n * L / t_copy / 1e9
     out = {"value": val, "unit": "GB/s",
            "h2d_bytes_per_step": tally["h2d"] // args.e2e_steps,
            "d2h_bytes_per_step": tally["d2h"] // args.e2e_steps,
            "steps": args.e2e_steps,
+           "link": {k: round(v, 1) for k, v in link.items()},
            "note": ("each timestep copied in once per step; every pair's blob and "
                     + ("reconstruction" if recon_out else "decode status word")
                     + " copied out; copies split over 4 streams each way and overlapped with "
@@ -677,27 +726,50 @@ def main():
     stream = torch.cuda.current_stream()
 
     n_pairs = len(COMBOS) * 3
+    blobs = [blob, torch.empty(bound, dtype=torch.uint8, device=dev)]
+    # (kind, events): "c" a compression (K1, K2, K3a+K3f, K3b, K3c), "s" a chained step (K41,
+    # then the same four), "d" a decompression (K4)
     ev_pool = []
 
-    def new_events(k):
+    def new_events(kind, k):
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
         for e in evs:          # torch creates the CUDA event on first record
             e.record(stream)
-        ev_pool.append(evs)
+        ev_pool.append((kind, evs))
         return evs
 
     def step(trace: bool):
         for E, B in combos:
-            prev = xs[0]
-            for t in range(1, 4):
+            if args.no_fuse:
+                prev = xs[0]
+                for t in range(1, 4):
+                    if trace:
+                        N.trace_events(new_events("c", 6))
+                    N.compress(prev, xs[t], E, B, blob=blobs[0], workspace=ws)
+                    if trace:
+                        N.trace_events(new_events("d", 2))
+                    out = recon[t % 2]
+                    N.decompress(blobs[0], prev, out=out, status=status)
+                    prev = out
+            else:
+                # timestep 1 compressed alone; timesteps 2 and 3 by the chained step, which also
+                # decompresses the blob before (Eq. 4: prev = that reconstruction); the last blob
+                # decompressed alone
                 if trace:
-                    N.trace_events(new_events(6))
-                N.compress(prev, xs[t], E, B, blob=blob, workspace=ws)
+                    N.trace_events(new_events("c", 6))
+                N.compress(xs[0], xs[1], E, B, blob=blobs[0], workspace=ws)
+                prev = xs[0]
+                for t in range(2, 4):
+                    out = recon[t % 2]
+                    if trace:
+                        N.trace_events(new_events("s", 6))
+                    N.decompress_compress(blobs[t % 2], prev, xs[t], E, B, out=out,
+                                          next_blob=blobs[(t + 1) % 2], workspace=ws,
+                                          status=status)
+                    prev = out
                 if trace:
-                    N.trace_events(new_events(2))
-                out = recon[t % 2]
-                N.decompress(blob, prev, out=out, status=status)
-                prev = out
+                    N.trace_events(new_events("d", 2))
+                N.decompress(blobs[0], prev, out=recon[0], status=status)
         if trace:
             N.trace_events(None)
 
@@ -726,37 +798,45 @@ def main():
     bytes_rank = args.steps * n_pairs * n * L
     value = _sum_over_ranks(dist, bytes_rank) / (ms_total / 1e3) / 1e9
 
-    # per-kernel times from the trace events: compress K1, K2, K3a, K3b, K3c; decompress K4
-    kt = {"k1_hist": 0.0, "k2_topk": 0.0, "k3_assign": 0.0, "k3_scan": 0.0, "k3_exact": 0.0,
-          "k4_decode": 0.0}
-    nc = nd = 0
-    for evs in ev_pool:
-        if len(evs) == 6:
-            for name, (a, b) in (("k1_hist", (0, 1)), ("k2_topk", (1, 2)), ("k3_assign", (2, 3)),
-                                 ("k3_scan", (3, 4)), ("k3_exact", (4, 5))):
-                kt[name] += evs[a].elapsed_time(evs[b])
-            nc += 1
+    # per-kernel times from the trace events
+    kt, kn = {}, {}
+    tail = (("k2_topk", 1, 2), ("k3_assign", 2, 3), ("k3_scan", 3, 4), ("k3_exact", 4, 5))
+
+    def add(name, ms):
+        kt[name] = kt.get(name, 0.0) + ms
+        kn[name] = kn.get(name, 0) + 1
+
+    for kind, evs in ev_pool:
+        if kind == "d":
+            add("k4_decode", evs[0].elapsed_time(evs[1]))
         else:
-            kt["k4_decode"] += evs[0].elapsed_time(evs[1])
-            nd += 1
-    avg = {k: (v / nd if k == "k4_decode" else v / nc) for k, v in kt.items()}
+            add("k1_hist" if kind == "c" else "k41_step", evs[0].elapsed_time(evs[1]))
+            for name, a, b in tail:
+                add(name, evs[a].elapsed_time(evs[b]))
+    avg = {k: kt[k] / kn[k] for k in kt}
     # algorithmic bytes per launch (HBM roofline); n_inc / B from the last blob of the step
-    hdr = N.parse_header(N.header_bytes(blob))
+    hdr = N.parse_header(N.header_bytes(blobs[0]))
     alpha = hdr["n_inc"] / n
     Bl = hdr["B"]
     # K1 reads p, x and writes a 2-byte code per point; K3a reads the codes and writes the
     # packed indices and 1 bit per point of incompressible flags; K3c reads the flags, gathers
     # the incompressible values of cur and writes them; K4 reads p (compressible points), the
-    # packed indices and the incompressible values and writes R.
+    # packed indices and the incompressible values and writes R; K41 does K4's traffic plus
+    # K1's without reading p (its p is the R it has just made)
     alg = {"k1_hist": 2 * L * n + 2 * n,
            "k3_assign": 2 * n + n * Bl / 8 + n / 8,
            "k3_exact": n / 8 + 2 * alpha * n * L,
            "k4_decode": (1 - alpha) * n * L + n * Bl / 8 + alpha * n * L + n * L}
+    alg["k41_step"] = alg["k4_decode"] + L * n + 2 * n
+    alg = {k: v for k, v in alg.items() if k in avg}
     dominant = max(alg, key=lambda k: avg[k])
     peak, peak_kind = _peaks()
     achieved = alg[dominant] / (avg[dominant] / 1e3) / 1e9
     kernel_ms = {k: round(v, 4) for k, v in avg.items()}
     kernel_gbs = {k: round(alg[k] / (avg[k] / 1e3) / 1e9, 1) for k in alg}
+    launches = {k: kn[k] // args.steps for k in kn}              # per step
+    step_alg = sum(alg[k] * launches[k] for k in alg)            # whole step, all kernels
+    # the compressions and decompressions run alone (every one without chaining)
     t_comp = sum(avg[k] for k in ("k1_hist", "k2_topk", "k3_assign", "k3_scan", "k3_exact"))
     comp_alg = alg["k1_hist"] + alg["k3_assign"] + alg["k3_exact"]
     one_pass = 2 * L * n + n * Bl / 8 + alpha * n * L      # read p, x once; write the blob once
@@ -788,20 +868,23 @@ def main():
             "config": {"workload": (WORKLOAD.replace("float64", "float32 (cast)").replace(
                            "8 GiB/step", "4 GiB/step") if args.f32 else WORKLOAD),
                        "n": n, "pairs_per_step": n_pairs,
+                       "chained": not args.no_fuse,
                        "l2": "inputs 8 GiB per array >> 129 MB L2: no flush",
                        "parallelism": f"replicas x{world} (independent series per GPU)"},
             "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": _traffic(dominant, side),
                          "algorithmic_bytes_per_launch": alg[dominant]},
-            "kernels_ms": kernel_ms, "kernels_gbs": kernel_gbs,
+            "kernels_ms": kernel_ms, "kernels_gbs": kernel_gbs, "launches_per_step": launches,
+            "step_hbm_frac": step_alg / (ms_step / 1e3) / 1e9 / peak,
             "compress_gbs": n * L / (t_comp / 1e3) / 1e9,
             "compress_path_hbm_frac": comp_alg / (t_comp / 1e3) / 1e9 / peak,
             "compress_one_pass_frac": one_pass / (t_comp / 1e3) / 1e9 / peak,
             "decompress_gbs": n * L / (avg["k4_decode"] / 1e3) / 1e9,
             "alpha_last": alpha, "B_last": Bl, "auto_b": bool(args.auto_b),
             "clocks": clk, "e2e": e2e, "e2e_blobs_only": e2e_blob, "cpu_baseline": cpu,
-            "gpu_launches": args.steps * n_pairs * (8 if args.auto_b else 7),
+            "gpu_launches": args.steps * len(COMBOS) * ((21 if args.no_fuse else 19)
+                                                        + (3 if args.auto_b else 0)),
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

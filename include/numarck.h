@@ -286,6 +286,32 @@ int numarck_decompress_range(const void* blob, const void* header_host,
                              const void* prev_seg, int64_t start, int64_t count,
                              void* out_seg, int32_t* status_dev, numarck_stream_t stream);
 
+/* ---- one step of a chain of timesteps (Eq. 4, §III.E; Eq. 1, §IV.B, §III.C) ----
+ * In a chain every timestep is compressed against the reconstruction of the previous one, so a
+ * decompression is followed by a compression whose prev is its output. This call queues both:
+ *   numarck_decompress(blob, header_host, prev, out, n, status_dev, stream), then
+ *   numarck_compress(out, next_cur, n, p, next_blob, next_blob_cap, ws, ws_bytes, stream),
+ * with the same results byte for byte. With the zero-centred grid (p->anchor ==
+ * NUMARCK_ANCHOR_ZERO) the decompression and the first pass of the compression (change ratio,
+ * bin, own-bin check, histogram) run as one kernel that classifies each reconstructed point
+ * while it is in registers, so out is written once and not read back. With
+ * NUMARCK_ANCHOR_MIN the grid origin needs the minimum ratio over all of out first, and the two
+ * run one after the other.
+ * blob, header_host, prev, status_dev : as for numarck_decompress; the blob must hold elements
+ *               of p->dtype (checked on the host when header_host is given, else on the
+ *               device).
+ * out         : device array of n elements of T: receives the reconstruction, which is also
+ *               the compression's prev. Must not overlap prev, blob, next_cur, next_blob or ws.
+ * next_cur, p, next_blob, next_blob_cap, ws, ws_bytes : as cur, p, blob, blob_cap, ws,
+ *               ws_bytes of numarck_compress (next_blob must not be blob).
+ * An error that the decompression finds on the device is stored into status_dev (if given)
+ * and also into next_blob's header status word, so that the next blob is refused too.
+ * Returns NUMARCK_OK once the work is queued, or the host-side errors of either call. */
+int numarck_decompress_compress(const void* blob, const void* header_host, const void* prev,
+                                void* out, int64_t n, int32_t* status_dev, const void* next_cur,
+                                const numarck_params* p, void* next_blob, size_t next_blob_cap,
+                                void* ws, size_t ws_bytes, numarck_stream_t stream);
+
 /* ---- batches of variables ----
  * The paper stores several compressed variables in one file (§IV.D); a checkpoint holds many
  * variables of different sizes, types, error bounds and index widths. A batch call compresses

@@ -254,12 +254,9 @@ int plan_compress(const void* prev, const void* cur, int64_t n, const numarck_pa
   return NUMARCK_OK;
 }
 
-// Queues the kernels of a planned compression on stream s (P.sms must be set).
-int launch_compress(const CompressPlan& P0, cudaStream_t s) {
-  trace(0, 6, s);
-  if (P0.g.anchor == NUMARCK_ANCHOR_MIN && launch_anchor_min(P0, s) != cudaSuccess)
-    return NUMARCK_ERR_CUDA;
-  if (launch_hist(P0, s) != cudaSuccess) return NUMARCK_ERR_CUDA;
+// Queues the kernels of a planned compression that follow K1 (its histogram, codes and bin
+// range are complete on stream s).
+int launch_compress_tail(const CompressPlan& P0, cudaStream_t s) {
   trace(1, 6, s);
   CompressPlan P = P0;
   if (P0.auto_b) {
@@ -294,6 +291,15 @@ int launch_compress(const CompressPlan& P0, cudaStream_t s) {
   if (launch_exact(P, s) != cudaSuccess) return NUMARCK_ERR_CUDA;
   trace(5, 6, s);
   return NUMARCK_OK;
+}
+
+// Queues the kernels of a planned compression on stream s (P.sms must be set).
+int launch_compress(const CompressPlan& P0, cudaStream_t s) {
+  trace(0, 6, s);
+  if (P0.g.anchor == NUMARCK_ANCHOR_MIN && launch_anchor_min(P0, s) != cudaSuccess)
+    return NUMARCK_ERR_CUDA;
+  if (launch_hist(P0, s) != cudaSuccess) return NUMARCK_ERR_CUDA;
+  return launch_compress_tail(P0, s);
 }
 
 int current_device_sms() { return device_sms(); }
@@ -372,6 +378,67 @@ int numarck_decompress_range(const void* blob, const void* header_host, const vo
                              int64_t start, int64_t count, void* out_seg, int32_t* status_dev,
                              numarck_stream_t stream) {
   return decode(blob, header_host, prev_seg, start, count, out_seg, -1, status_dev, stream);
+}
+
+int numarck_decompress_compress(const void* blob, const void* header_host, const void* prev,
+                                void* out, int64_t n, int32_t* status_dev, const void* next_cur,
+                                const numarck_params* p, void* next_blob, size_t next_blob_cap,
+                                void* ws, size_t ws_bytes, numarck_stream_t stream) {
+  if (n < 0) return NUMARCK_ERR_INVALID_ARG;
+  int rc = plan_decompress_check(blob, prev, out, n);
+  if (rc) return rc;
+  CompressPlan P;
+  rc = plan_compress(out, next_cur, n, p, next_blob, next_blob_cap, ws, ws_bytes, &P);
+  if (rc) return rc;
+  int64_t ntiles = 0;
+  if (header_host) {
+    numarck_header h;
+    std::memcpy(&h, header_host, sizeof(h));
+    Geometry g;
+    rc = check_header(h, &g);
+    if (rc) return rc;
+    if (h.n != n || h.dtype != p->dtype) return NUMARCK_ERR_INVALID_ARG;
+    ntiles = g.nsub;
+  }
+  const size_t L = p->dtype == NUMARCK_F64 ? 8 : 4;
+  auto overlap = [](const void* a, size_t na, const void* b, size_t nb) {
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return na && nb && x < y + nb && y < x + na;
+  };
+  const size_t nb = (size_t)n * L;
+  if (blob == next_blob || overlap(out, nb, prev, nb) || overlap(out, nb, next_cur, nb) ||
+      overlap(out, nb, next_blob, next_blob_cap) || overlap(out, nb, ws, ws_bytes) ||
+      overlap(out, nb, blob, NUMARCK_HEADER_BYTES))
+    return NUMARCK_ERR_INVALID_ARG;
+  if (P.auto_b) {   // as numarck_compress: choosing B synchronises, not allowed while capturing
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(reinterpret_cast<cudaStream_t>(stream), &cs) != cudaSuccess)
+      return NUMARCK_ERR_CUDA;
+    if (cs != cudaStreamCaptureStatusNone) return NUMARCK_ERR_INVALID_ARG;
+  }
+  P.sms = device_sms();
+  if (P.sms <= 0) return NUMARCK_ERR_CUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (n == 0) return launch_compress(P, s);
+  DecodePlan D{};
+  D.blob = static_cast<const unsigned char*>(blob);
+  D.prev_seg = prev;
+  D.out_seg = out;
+  D.status = status_dev;
+  D.start = 0;
+  D.count = n;
+  D.n_expected = n;
+  D.ntiles_hint = ntiles;
+  D.sms = P.sms;
+  D.status2 = &reinterpret_cast<Ctrl*>(P.ws + P.wl.ctrl)->error;
+  D.dtype = p->dtype;
+  if (p->anchor == NUMARCK_ANCHOR_MIN) {
+    if (launch_decode(D, s) != cudaSuccess) return NUMARCK_ERR_CUDA;
+    return launch_compress(P, s);
+  }
+  trace(0, 6, s);
+  if (launch_step(D, P, s) != cudaSuccess) return NUMARCK_ERR_CUDA;
+  return launch_compress_tail(P, s);
 }
 
 int numarck_trace_events(void* const* events, int count) {

@@ -1,0 +1,102 @@
+// k4.cuh — the pieces of K4 (decompression, §III.E with Eq. 4 read as R = prev * (1 + centre))
+// shared by the decode kernel (k_decode.cu) and the fused decompress-and-classify kernel
+// (k_step.cu): vector loads and stores, and the B-bit field of a lane in a 128-element step.
+#pragma once
+
+#include <type_traits>
+
+#include "launch.h"
+
+namespace nmk {
+
+struct DecodeArgs {
+  const unsigned char* blob;
+  const void* prev_seg;
+  void* out_seg;
+  int32_t* status;
+  long long start, count, n_expected;
+  int* status2;              // a second error word (the next compression's), or null
+  int dtype;                 // NUMARCK_F32 / NUMARCK_F64 the blob must hold, or 0 for either
+};
+
+// An error found on the device goes to both status words (either may be null).
+__device__ __forceinline__ void report(const DecodeArgs& A, int rc) {
+  if (A.status) atomicExch(A.status, rc);
+  if (A.status2) atomicExch(A.status2, rc);
+}
+
+template <typename T>
+struct BitsOf;
+template <>
+struct BitsOf<float> {
+  using U = unsigned int;
+  __device__ __forceinline__ static float as(U u) { return __uint_as_float(u); }
+};
+template <>
+struct BitsOf<double> {
+  using U = unsigned long long;
+  __device__ __forceinline__ static double as(U u) { return __longlong_as_double((long long)u); }
+};
+
+// Four consecutive T as 16-byte vectors (16-byte aligned addresses).
+__device__ __forceinline__ void ld4(const double* p, double* v) {
+  const double2 a = __ldcs(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldcs(reinterpret_cast<const double2*>(p) + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void ld4(const float* p, float* v) {
+  const float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void st4(double* p, const double* v) {
+  __stcs(reinterpret_cast<double2*>(p), make_double2(v[0], v[1]));
+  __stcs(reinterpret_cast<double2*>(p) + 1, make_double2(v[2], v[3]));
+}
+__device__ __forceinline__ void st4(float* p, const float* v) {
+  __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+}
+
+constexpr int K4_WARPS = 16;                    // warps per CTA (each owns whole tiles)
+constexpr int K4_THREADS = K4_WARPS * 32;
+constexpr int K4_SEG = 128;                     // elements per warp step: 4 consecutive per lane
+// steps whose loads are in flight together: float32 moves half the bytes per load, so it
+// keeps two steps in flight to have as many bytes outstanding as float64 with one
+template <typename T>
+__host__ __device__ constexpr int k4_unroll() { return sizeof(T) == 4 ? 2 : 1; }
+
+template <int B>
+struct Field {
+  using type = typename std::conditional<(4 * B <= 32), unsigned, unsigned long long>::type;
+};
+
+// The 4B-bit field of lane `lane` in the step whose image starts at word ws of the tile image
+// tw (twords words). Words past the image read as 0.
+template <int B>
+__device__ __forceinline__ typename Field<B>::type load_field(const unsigned* tw, int twords,
+                                                              int ws, int lane) {
+  constexpr int FB = 4 * B;
+  using F = typename Field<B>::type;
+  if constexpr (FB == 32) {
+    const int w = ws + lane;
+    return w < twords ? __ldg(tw + w) : 0u;
+  } else if constexpr (FB == 64) {
+    const int w = ws + 2 * lane;                 // twords is even: both words or neither
+    if (w >= twords) return 0ull;
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(tw + w));
+    return (unsigned long long)v.x | ((unsigned long long)v.y << 32);
+  } else {
+    const int bit = FB * lane;
+    const int w0 = ws + (bit >> 5), o = bit & 31;
+    const unsigned a0 = w0 < twords ? __ldg(tw + w0) : 0u;
+    const unsigned a1 = (o + FB > 32 && w0 + 1 < twords) ? __ldg(tw + w0 + 1) : 0u;
+    const unsigned long long v = (unsigned long long)a0 | ((unsigned long long)a1 << 32);
+    if constexpr (FB > 32) {
+      const unsigned a2 = (o + FB > 64 && w0 + 2 < twords) ? __ldg(tw + w0 + 2) : 0u;
+      return (F)((v >> o) | (o ? ((unsigned long long)a2 << (64 - o)) : 0ull));
+    } else {
+      return (F)(v >> o);
+    }
+  }
+}
+
+}  // namespace nmk

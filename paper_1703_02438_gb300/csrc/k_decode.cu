@@ -17,95 +17,11 @@
 // The kernel reads the blob header from device memory and validates it (magic, version, status
 // word, geometry implied by n/B/block size, counts), so decompression needs no host round trip
 // after compression: a compress -> decompress chain stays asynchronous on one stream.
-#include <type_traits>
-
-#include "launch.h"
+#include "k4.cuh"
 
 namespace nmk {
 
 namespace {
-
-struct DecodeArgs {
-  const unsigned char* blob;
-  const void* prev_seg;
-  void* out_seg;
-  int32_t* status;
-  long long start, count, n_expected;
-};
-
-template <typename T>
-struct BitsOf;
-template <>
-struct BitsOf<float> {
-  using U = unsigned int;
-  __device__ __forceinline__ static float as(U u) { return __uint_as_float(u); }
-};
-template <>
-struct BitsOf<double> {
-  using U = unsigned long long;
-  __device__ __forceinline__ static double as(U u) { return __longlong_as_double((long long)u); }
-};
-
-// Four consecutive T as 16-byte vectors (16-byte aligned addresses).
-__device__ __forceinline__ void ld4(const double* p, double* v) {
-  const double2 a = __ldcs(reinterpret_cast<const double2*>(p));
-  const double2 b = __ldcs(reinterpret_cast<const double2*>(p) + 1);
-  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-}
-__device__ __forceinline__ void ld4(const float* p, float* v) {
-  const float4 a = __ldcs(reinterpret_cast<const float4*>(p));
-  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-}
-__device__ __forceinline__ void st4(double* p, const double* v) {
-  __stcs(reinterpret_cast<double2*>(p), make_double2(v[0], v[1]));
-  __stcs(reinterpret_cast<double2*>(p) + 1, make_double2(v[2], v[3]));
-}
-__device__ __forceinline__ void st4(float* p, const float* v) {
-  __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
-}
-
-constexpr int K4_WARPS = 16;                    // warps per CTA (each owns whole tiles)
-constexpr int K4_THREADS = K4_WARPS * 32;
-constexpr int K4_SEG = 128;                     // elements per warp step: 4 consecutive per lane
-// steps whose loads are in flight together: float32 moves half the bytes per load, so it
-// keeps two steps in flight to have as many bytes outstanding as float64 with one
-template <typename T>
-__host__ __device__ constexpr int k4_unroll() { return sizeof(T) == 4 ? 2 : 1; }
-
-template <int B>
-struct Field {
-  using type = typename std::conditional<(4 * B <= 32), unsigned, unsigned long long>::type;
-};
-
-// The 4B-bit field of lane `lane` in the step whose image starts at word ws of the tile image
-// tw (twords words). Words past the image read as 0.
-template <int B>
-__device__ __forceinline__ typename Field<B>::type load_field(const unsigned* tw, int twords,
-                                                              int ws, int lane) {
-  constexpr int FB = 4 * B;
-  using F = typename Field<B>::type;
-  if constexpr (FB == 32) {
-    const int w = ws + lane;
-    return w < twords ? __ldg(tw + w) : 0u;
-  } else if constexpr (FB == 64) {
-    const int w = ws + 2 * lane;                 // twords is even: both words or neither
-    if (w >= twords) return 0ull;
-    const uint2 v = __ldg(reinterpret_cast<const uint2*>(tw + w));
-    return (unsigned long long)v.x | ((unsigned long long)v.y << 32);
-  } else {
-    const int bit = FB * lane;
-    const int w0 = ws + (bit >> 5), o = bit & 31;
-    const unsigned a0 = w0 < twords ? __ldg(tw + w0) : 0u;
-    const unsigned a1 = (o + FB > 32 && w0 + 1 < twords) ? __ldg(tw + w0 + 1) : 0u;
-    const unsigned long long v = (unsigned long long)a0 | ((unsigned long long)a1 << 32);
-    if constexpr (FB > 32) {
-      const unsigned a2 = (o + FB > 64 && w0 + 2 < twords) ? __ldg(tw + w0 + 2) : 0u;
-      return (F)((v >> o) | (o ? ((unsigned long long)a2 << (64 - o)) : 0ull));
-    } else {
-      return (F)(v >> o);
-    }
-  }
-}
 
 template <typename T, int B>
 __device__ __forceinline__ void decode_tiles(const DecodeArgs& A, const Geometry& g,
@@ -139,7 +55,7 @@ __device__ __forceinline__ void decode_tiles(const DecodeArgs& A, const Geometry
     const int twords = 4 * ((cnt * B + 127) / 128);
     if (base < 0 || base > n_inc || (boff & 15) || boff < 0 ||
         tstart + 4LL * twords > g.index_bytes) {
-      if (lane == 0 && A.status) atomicExch(A.status, NUMARCK_ERR_CORRUPT);
+      if (lane == 0) report(A, NUMARCK_ERR_CORRUPT);
       continue;
     }
     const unsigned* tw = reinterpret_cast<const unsigned*>(index + tstart);
@@ -195,8 +111,8 @@ __device__ __forceinline__ void decode_tiles(const DecodeArgs& A, const Geometry
             const long long pos = run + before + __popc(nib & ((1u << k) - 1u));
             U v = 0;
             if (pos < n_inc) v = exact_u[pos];
-            else if (A.status && e0 + k >= e_lo && e0 + k < e_hi)
-              atomicExch(A.status, NUMARCK_ERR_CORRUPT);
+            else if (e0 + k >= e_lo && e0 + k < e_hi)
+              report(A, NUMARCK_ERR_CORRUPT);
             r[k] = BitsOf<T>::as(v);
           } else {
             T m;
@@ -215,9 +131,9 @@ __device__ __forceinline__ void decode_tiles(const DecodeArgs& A, const Geometry
         }
       }
     }
-    if (e_hi == cnt && lane == 0 && A.status) {
+    if (e_hi == cnt && lane == 0) {
       const long long next = (gt + 1 < g.nsub) ? sub_off[gt + 1] : n_inc;
-      if (run != next) atomicExch(A.status, NUMARCK_ERR_CORRUPT);
+      if (run != next) report(A, NUMARCK_ERR_CORRUPT);
     }
   }
 }
@@ -247,6 +163,7 @@ __global__ void __launch_bounds__(K4_THREADS, 2) k4_decode(DecodeArgs A) {
     Geometry g{};
     int rc = check_header(s_h, &g);
     if (!rc && A.n_expected >= 0 && A.n_expected != s_h.n) rc = NUMARCK_ERR_INVALID_ARG;
+    if (!rc && A.dtype && A.dtype != s_h.dtype) rc = NUMARCK_ERR_INVALID_ARG;
     if (!rc && (A.start < 0 || A.count < 0 || A.start > s_h.n || A.count > s_h.n - A.start))
       rc = NUMARCK_ERR_RANGE;
     const unsigned L = s_h.dtype == NUMARCK_F64 ? 8u : 4u;
@@ -258,7 +175,7 @@ __global__ void __launch_bounds__(K4_THREADS, 2) k4_decode(DecodeArgs A) {
       g0 = q0 * g.spb + (first - q0 * g.epb) / SUB;
       g1 = q1 * g.spb + (last - q1 * g.epb) / SUB;
     }
-    if (rc && blockIdx.x == 0 && A.status) atomicExch(A.status, rc);
+    if (rc && blockIdx.x == 0) report(A, rc);
     s_ok = rc == 0 && g1 >= g0 + (long long)blockIdx.x * K4_WARPS;
     s_g = g;
     s_g0 = g0;
@@ -302,7 +219,8 @@ cudaError_t launch_decode(const DecodePlan& P, cudaStream_t s) {
     const long long need = (P.ntiles_hint + K4_WARPS - 1) / K4_WARPS;
     if (blocks > need) blocks = need;
   }
-  DecodeArgs A{P.blob, P.prev_seg, P.out_seg, P.status, P.start, P.count, P.n_expected};
+  DecodeArgs A{P.blob, P.prev_seg, P.out_seg, P.status, P.start, P.count, P.n_expected, P.status2,
+               P.dtype};
   k4_decode<<<(int)blocks, K4_THREADS, 0, s>>>(A);
   return cudaGetLastError();
 }

@@ -1,0 +1,270 @@
+// k_step.cu — K41: one step of the closed loop in one kernel, the decompression of a blob (K4)
+// fused with the first pass of the next compression (K1) against the reconstruction it makes.
+//
+// In the paper's in-situ use every new timestep is compressed against the reconstruction of the
+// previous one (Eq. 4 chains R_i = R_{i-1} (1 + c), §III.E), so a decompression is followed by
+// a compression whose prev is that decompression's output. Run one after the other, K4 writes
+// R to HBM and K1 reads it back. Here each lane classifies the four points it has just
+// reconstructed (Eq. 1 ratio, §IV.B.1 bin and histogram, §III.C own-bin check, 16-bit code)
+// while they are still in registers, and reads only the next timestep besides: the step moves
+// (1-α)L + B/8 + αL + L (decompression) + L + 2 (classification) bytes per point instead of
+// that plus another L. K4 alone waits on memory and K1 alone on ALU issue, so in one kernel the
+// two halves also overlap within each SM. Every output equals that of K4 followed by K1: the
+// reconstruction, the codes, the histogram and the bin range.
+//
+// Used for the zero-centred grid only (the paper-literal grid anchored at the minimum ratio
+// needs that minimum over all of R before any bin is known).
+#include <algorithm>
+
+#include "k1.cuh"
+#include "k4.cuh"
+
+namespace nmk {
+
+namespace {
+
+struct StepArgs {
+  const void* cur;               // the next timestep, n elements of T
+  Ctrl* ctrl;                    // the next compression's control block
+  unsigned long long* hist;      // its global histogram window
+  unsigned long long* tstatus;   // its per-tile counts and offset-scan flags
+  int64_t nsub;                  // its sub-block count
+  unsigned short* codes;         // its per-point codes
+};
+
+template <typename T, int B>
+__device__ __forceinline__ void step_tiles(const DecodeArgs& A, const StepArgs& S,
+                                           const Geometry& g, long long n_inc, const T* s_m,
+                                           const Consts<T>& c, const HistCtx& h, int& lmin,
+                                           int& lmax) {
+  using U = typename BitsOf<T>::U;
+  using F = typename Field<B>::type;
+  constexpr int FB = 4 * B;
+  constexpr unsigned M = (1u << B) - 1u;
+  const int lane = (int)lane_id();
+  const int warp = (int)(threadIdx.x >> 5);
+  const T* centres = reinterpret_cast<const T*>(A.blob + g.off_centres);
+  const int64_t* idx_off = reinterpret_cast<const int64_t*>(A.blob + g.off_idx_off);
+  const int64_t* sub_off = reinterpret_cast<const int64_t*>(A.blob + g.off_sub_off);
+  const U* exact_u = reinterpret_cast<const U*>(A.blob + g.off_exact);
+  const unsigned char* index = A.blob + g.off_index;
+  const T* prev = static_cast<const T*>(A.prev_seg);
+  T* out = static_cast<T*>(A.out_seg);
+  const T* cur = static_cast<const T*>(S.cur);
+  const unsigned lt = lanemask_lt();
+
+  const long long W = (long long)gridDim.x * K4_WARPS;
+  for (long long gt = (long long)blockIdx.x * K4_WARPS + warp; gt < g.nsub; gt += W) {
+    const long long q = gt / g.spb, t = gt - q * g.spb;
+    const long long j0 = q * g.epb + t * SUB;
+    const long long bend = min((long long)g.n, (long long)((q + 1) * g.epb));
+    const int cnt = (int)min((long long)SUB, bend - j0);
+    const long long base = sub_off[gt];
+    const long long boff = idx_off[q];
+    const long long tstart = boff + t * (long long)(SUB / 8 * B);
+    const int twords = 4 * ((cnt * B + 127) / 128);
+    if (base < 0 || base > n_inc || (boff & 15) || boff < 0 ||
+        tstart + 4LL * twords > g.index_bytes) {
+      if (lane == 0) report(A, NUMARCK_ERR_CORRUPT);
+      continue;
+    }
+    const unsigned* tw = reinterpret_cast<const unsigned*>(index + tstart);
+    const T* pt = prev + j0;
+    T* ot = out + j0;
+    const T* xt = cur + j0;
+    unsigned short* ct = S.codes + j0;
+    const bool vec = ((reinterpret_cast<uintptr_t>(pt) | reinterpret_cast<uintptr_t>(ot) |
+                       reinterpret_cast<uintptr_t>(xt)) & 15) == 0;
+    const bool cvec = (reinterpret_cast<uintptr_t>(ct) & 7) == 0;
+    long long run = base;
+    for (int s0 = 0; s0 < cnt; s0 += K4_SEG) {
+      const int e0 = s0 + 4 * lane;
+      const bool whole = s0 + K4_SEG <= cnt;     // uniform across the warp
+      const F field = load_field<B>(tw, twords, (s0 / K4_SEG) * FB, lane);
+      T pv[4], xv[4];
+      if (vec && whole) {
+        ld4(pt + e0, pv);
+        ld4(xt + e0, xv);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          pv[k] = e0 + k < cnt ? __ldcs(pt + e0 + k) : (T)0;
+          xv[k] = e0 + k < cnt ? __ldcs(xt + e0 + k) : (T)0;
+        }
+      }
+      // decompression of the four points (as K4)
+      unsigned id[4];
+      unsigned nib = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        id[k] = (unsigned)(field >> (k * B)) & M;
+        nib |= (e0 + k < cnt && id[k] == M) ? (1u << k) : 0u;
+      }
+      unsigned before = 0, total = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const unsigned bk = __ballot_sync(0xffffffffu, (nib >> k) & 1u);
+        before += __popc(bk & lt);
+        total += __popc(bk);
+      }
+      T r[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if ((nib >> k) & 1u) {
+          const long long pos = run + before + __popc(nib & ((1u << k) - 1u));
+          U v = 0;
+          if (pos < n_inc) v = exact_u[pos];
+          else report(A, NUMARCK_ERR_CORRUPT);
+          r[k] = BitsOf<T>::as(v);
+        } else {
+          T m;
+          if constexpr ((1 << B) <= DM_SMEM) m = s_m[id[k]];
+          else m = id[k] < (unsigned)DM_SMEM ? s_m[id[k]] : t_add((T)1, centres[id[k]]);
+          r[k] = t_mul(pv[k], m);
+        }
+      }
+      run += total;
+      if (vec && whole) {
+        st4(ot + e0, r);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (e0 + k < cnt) ot[e0 + k] = r[k];
+      }
+      // first pass of the next compression on (r, x) (as K1)
+      unsigned pend = 0;
+      unsigned cw[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        int b = 0;
+        bool pass = false;
+        const int kind = e0 + k < cnt ? Classifier<T>::fast(r[k], xv[k], c, h.cbase, b, pass) : 0;
+        const bool binned = kind == 1;
+        if (kind >= 2) pend |= 1u << k;
+        cw[k] = bin_code(h, binned, b, pass);
+        hist_add(h, binned, b, lmin, lmax);
+      }
+      if (cvec && whole) {
+        *reinterpret_cast<uint2*>(ct + e0) = make_uint2(cw[0] | (cw[1] << 16), cw[2] | (cw[3] << 16));
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (e0 + k < cnt) ct[e0 + k] = (unsigned short)cw[k];
+      }
+      // undecided points (rare): the exact sequences, one per lane per round; the point's
+      // reconstruction is read back from this lane's own store
+      while (__any_sync(0xffffffffu, pend != 0u)) {
+        int b = 0;
+        bool binned = false, pass = false;
+        if (pend) {
+          const int k = __ffs(pend) - 1;
+          pend &= pend - 1;
+          binned = Classifier<T>::exact(ot[e0 + k], xt[e0 + k], c, h.cbase, b, pass) == 1;
+          ct[e0 + k] = (unsigned short)bin_code(h, binned, b, pass);
+        }
+        hist_add(h, binned, b, lmin, lmax);
+      }
+    }
+    if (lane == 0) {
+      const long long next = (gt + 1 < g.nsub) ? sub_off[gt + 1] : n_inc;
+      if (run != next) report(A, NUMARCK_ERR_CORRUPT);
+    }
+  }
+}
+
+template <typename T, int B = 1>
+__device__ __forceinline__ void step_dispatch(const DecodeArgs& A, const StepArgs& S,
+                                              const Geometry& g, long long n_inc, const T* s_m,
+                                              const Consts<T>& c, const HistCtx& h, int& lmin,
+                                              int& lmax) {
+  if constexpr (B <= NUMARCK_MAX_B) {
+    if (g.B == B)
+      step_tiles<T, B>(A, S, g, n_inc, s_m, c, h, lmin, lmax);
+    else
+      step_dispatch<T, B + 1>(A, S, g, n_inc, s_m, c, h, lmin, lmax);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(K4_THREADS, 2) k41_step(DecodeArgs A, StepArgs S, Consts<T> c) {
+  extern __shared__ unsigned int sh[];                           // K1's shared window
+  __shared__ __align__(16) unsigned char s_tab[DM_SMEM * 8];     // multipliers m = 1 + centre
+  __shared__ __align__(16) numarck_header s_h;
+  __shared__ Geometry s_g;
+  __shared__ int s_rc;
+  // zero-centred grid: the zero-change bin is 0, the centre of the shared window
+  const HistCtx h{sh, S.hist, S.ctrl, -SH_BINS / 2, c.hbase, -CODE_HALF, S.codes};
+  if (threadIdx.x < NUMARCK_HEADER_BYTES / 16)
+    reinterpret_cast<uint4*>(&s_h)[threadIdx.x] = reinterpret_cast<const uint4*>(A.blob)[threadIdx.x];
+  k1_begin(h, S.tstatus, S.nsub);                                // ends with a block barrier
+  if (threadIdx.x == 0) {
+    Geometry g{};
+    int rc = check_header(s_h, &g);
+    if (!rc && s_h.n != A.n_expected) rc = NUMARCK_ERR_INVALID_ARG;
+    if (!rc && s_h.dtype != A.dtype) rc = NUMARCK_ERR_INVALID_ARG;
+    if (rc && blockIdx.x == 0) report(A, rc);
+    s_rc = rc;
+    s_g = g;
+  }
+  __syncthreads();
+  int lmin = 0x7FFFFFFF, lmax = (int)0x80000000;
+  if (s_rc) {
+    // no reconstruction to classify: every point of the next compression is left not binnable
+    // (its blob carries the error in its header)
+    unsigned short* codes = S.codes;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < A.n_expected;
+         j += (long long)gridDim.x * blockDim.x)
+      codes[j] = (unsigned short)CODE_NONE;
+  } else {
+    const Geometry g = s_g;
+    const int nm = min(1 << g.B, DM_SMEM);
+    T* s_m = reinterpret_cast<T*>(s_tab);
+    const T* centres = reinterpret_cast<const T*>(A.blob + g.off_centres);
+    for (int r = threadIdx.x; r < nm; r += K4_THREADS) s_m[r] = t_add((T)1, centres[r]);
+    __syncthreads();
+    step_dispatch<T>(A, S, g, s_h.n_inc, s_m, c, h, lmin, lmax);
+  }
+  k1_end(h, lmin, lmax);
+}
+
+template <typename T>
+cudaError_t launch_step_t(const DecodePlan& D, const CompressPlan& P, cudaStream_t s) {
+  static int occ[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const size_t smem = SH_BINS * sizeof(unsigned int);
+  int per_sm = dev < 64 ? occ[dev] : 0;
+  if (per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k41_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k41_step<T>, K4_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (dev < 64) occ[dev] = per_sm;
+  }
+  // one wave of resident CTAs, fewer when the decompressed blob has fewer tiles (its tile count
+  // when its header was given on the host, else the least it can have)
+  long long blocks = (long long)P.sms * per_sm;
+  const long long tiles = D.ntiles_hint > 0 ? D.ntiles_hint : (D.count + SUB - 1) / SUB;
+  blocks = std::min(blocks, std::max(1LL, (tiles + K4_WARPS - 1) / K4_WARPS));
+  Ctrl* ctrl = reinterpret_cast<Ctrl*>(P.ws + P.wl.ctrl);
+  DecodeArgs A{D.blob, D.prev_seg, D.out_seg, D.status, 0, D.count, D.n_expected, &ctrl->error,
+               P.g.dtype};
+  StepArgs S{P.cur, ctrl, reinterpret_cast<unsigned long long*>(P.ws + P.wl.hist),
+             reinterpret_cast<unsigned long long*>(P.ws + P.wl.status), P.g.nsub,
+             reinterpret_cast<unsigned short*>(P.blob + P.code_off)};
+  if constexpr (sizeof(T) == 8)
+    k41_step<double><<<(int)blocks, K4_THREADS, smem, s>>>(A, S, P.cd);
+  else
+    k41_step<float><<<(int)blocks, K4_THREADS, smem, s>>>(A, S, P.cf);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_step(const DecodePlan& D, const CompressPlan& P, cudaStream_t s) {
+  return P.g.dtype == NUMARCK_F64 ? launch_step_t<double>(D, P, s) : launch_step_t<float>(D, P, s);
+}
+
+}  // namespace nmk

@@ -252,6 +252,8 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_topk(TopkArgs A, Consts<T> c
   const int i0 = bmin - c.hbase;
   int status = 0;
   if (any && (i0 < 0 || i0 + R > HWIN || ctrl->win_err)) { status = NUMARCK_ERR_CORRUPT; R = 0; }
+  // an error of the decompression that made this compression's prev (fused step) marks the blob
+  if (ctrl->error) status = ctrl->error;
   unsigned long long* H = A.hist + (any ? i0 : 0);
   const int k = (1 << g.B) - 1;
   const int M = g.M;
@@ -359,6 +361,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_topk(TopkArgs A, Consts<T> c
     ctrl->bmax_key = 0u;
     ctrl->amin_key = 0ull;
     ctrl->win_err = 0u;
+    ctrl->error = 0;
     ctrl->any = any && R > 0;
     ctrl->sel_bmin = bmin;
     ctrl->sel_bmax = bmax;

@@ -33,6 +33,8 @@ struct DecodePlan {
   int64_t start, count, n_expected;
   int64_t ntiles_hint;
   int sms;
+  int* status2;            // optional second error word (the next compression's Ctrl::error)
+  int dtype;               // element type the blob must hold (0: either)
 };
 
 cudaError_t launch_anchor_min(const CompressPlan& P, cudaStream_t s);  // K0 (ANCHOR_MIN only)
@@ -52,11 +54,15 @@ cudaError_t launch_assign(const CompressPlan& P, cudaStream_t s);      // K3a: i
 cudaError_t launch_offsets(const CompressPlan& P, cudaStream_t s);     // K3b: offset tables
 cudaError_t launch_exact(const CompressPlan& P, cudaStream_t s);       // K3c: incompressible values
 cudaError_t launch_decode(const DecodePlan& P, cudaStream_t s);        // K4 / K5
+// K41: decompression of D fused with K1 of the compression P of a new timestep against D's
+// output (zero-centred grid only)
+cudaError_t launch_step(const DecodePlan& D, const CompressPlan& P, cudaStream_t s);
 
 // Host-side planning shared by the single-variable and batched entry points (capi.cu).
 int plan_compress(const void* prev, const void* cur, int64_t n, const numarck_params* p,
                   void* blob, size_t blob_cap, void* ws, size_t ws_bytes, CompressPlan* out);
 int launch_compress(const CompressPlan& P, cudaStream_t s);
+int launch_compress_tail(const CompressPlan& P, cudaStream_t s);   // everything after K1
 int plan_decompress_check(const void* blob, const void* prev, void* out, int64_t n);
 int launch_decompress(const void* blob, const void* prev, void* out, int64_t n, int32_t* status,
                       int sms, cudaStream_t s);

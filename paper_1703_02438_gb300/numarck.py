@@ -119,6 +119,9 @@ def lib() -> ctypes.CDLL:
         L.numarck_decompress.restype = i32
         L.numarck_decompress_range.argtypes = [vp, vp, vp, i64, i64, vp, vp, vp]
         L.numarck_decompress_range.restype = i32
+        L.numarck_decompress_compress.argtypes = [vp, vp, vp, vp, i64, vp, vp, pp, vp, sz, vp, sz,
+                                                   vp]
+        L.numarck_decompress_compress.restype = i32
         L.numarck_status_string.argtypes = [i32]
         L.numarck_status_string.restype = ctypes.c_char_p
         L.numarck_trace_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), i32]
@@ -284,6 +287,41 @@ def decompress_range(blob: torch.Tensor, prev_seg: torch.Tensor, start: int, cou
                                           ctypes.c_void_p(_stream_ptr(stream))),
            "numarck_decompress_range")
     return out
+
+
+def decompress_compress(blob: torch.Tensor, prev: torch.Tensor, next_cur: torch.Tensor, E: float,
+                        B: int, anchor: int = ANCHOR_ZERO, block_bytes: int = 0,
+                        out: torch.Tensor | None = None, next_blob: torch.Tensor | None = None,
+                        workspace: Workspace | None = None, status: torch.Tensor | None = None,
+                        header: bytes | None = None, stream=None):
+    """One step of a chain of timesteps: decompresses `blob` (compressed against `prev`) into
+    `out` and queues the compression of `next_cur` against `out` into `next_blob`
+    (numarck_decompress_compress). Returns (out, next_blob)."""
+    if prev.dtype != next_cur.dtype or prev.shape != next_cur.shape or prev.dim() != 1:
+        raise ValueError("prev and next_cur must be 1-D tensors of the same dtype and length")
+    if not (prev.is_cuda and next_cur.is_cuda and blob.is_cuda):
+        raise ValueError("blob, prev and next_cur must be CUDA tensors")
+    prev = prev.contiguous()
+    next_cur = next_cur.contiguous()
+    params = make_params(prev.dtype, B, E, anchor, block_bytes)
+    n = prev.numel()
+    bound = compress_bound(n, params)
+    if bound == 0:
+        raise NumarckError(ERR_INVALID_ARG, "numarck_compress_bound")
+    if out is None:
+        out = torch.empty_like(prev)
+    if next_blob is None:
+        next_blob = torch.empty(bound, dtype=torch.uint8, device=prev.device)
+    ws = (workspace or _workspace_for(prev.device)).get(workspace_bytes(n, params), stream)
+    hp = ctypes.c_char_p(header) if header is not None else None
+    sp = ctypes.c_void_p(status.data_ptr()) if status is not None else None
+    _check(lib().numarck_decompress_compress(
+        ctypes.c_void_p(blob.data_ptr()), hp, ctypes.c_void_p(prev.data_ptr()),
+        ctypes.c_void_p(out.data_ptr()), n, sp, ctypes.c_void_p(next_cur.data_ptr()),
+        ctypes.byref(params), ctypes.c_void_p(next_blob.data_ptr()), next_blob.numel(),
+        ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(_stream_ptr(stream))),
+        "numarck_decompress_compress")
+    return out, next_blob
 
 
 class Batch:

@@ -156,6 +156,36 @@ def test_decompress_argument_errors_before_device(lib):
                                   ctypes.c_void_p(A), 5000, None, None) == N.ERR_INVALID_ARG
 
 
+def test_chained_step_argument_errors_before_device(lib):
+    """numarck_decompress_compress validates both halves, the blob header against the
+    parameters and the aliasing of its buffers on the host, before any CUDA call."""
+    n = 5000
+    data = _oracle_header(n=n)
+    hb = ctypes.c_char_p(data[:256])
+    p = N.Params(N.F64, 8, 1e-3, 0, 0, 0)
+    bound, wsb = N.compress_bound(n, p), N.workspace_bytes(n, p)
+    blob, prev, out, cur, nblob, ws = (k << 30 for k in range(1, 7))   # disjoint fake buffers
+    C = lambda blob=blob, prev=prev, out=out, cur=cur, nblob=nblob, ws=ws, n=n, pp=p, hb=hb: \
+        lib.numarck_decompress_compress(
+            ctypes.c_void_p(blob), hb, ctypes.c_void_p(prev), ctypes.c_void_p(out), n, None,
+            ctypes.c_void_p(cur), ctypes.byref(pp), ctypes.c_void_p(nblob), bound,
+            ctypes.c_void_p(ws), wsb, None)
+    assert C(n=-1) == N.ERR_INVALID_ARG
+    assert C(blob=blob + 16) == N.ERR_INVALID_ARG                    # blob not 256-aligned
+    assert C(out=0) == N.ERR_INVALID_ARG
+    assert C(nblob=blob) == N.ERR_INVALID_ARG                        # next blob = this blob
+    assert C(out=nblob + 256) == N.ERR_INVALID_ARG                   # out inside the next blob
+    assert C(out=ws) == N.ERR_INVALID_ARG                            # out inside the workspace
+    assert C(out=cur + 8) == N.ERR_INVALID_ARG                       # out overlaps next_cur
+    assert C(out=prev) == N.ERR_INVALID_ARG                          # out is prev
+    assert C(n=n - 1) == N.ERR_INVALID_ARG                           # n differs from the header
+    p32 = N.Params(N.F32, 8, 1e-3, 0, 0, 0)
+    assert C(pp=p32) == N.ERR_INVALID_ARG                            # float64 blob, float32 step
+    bad = bytearray(data[:256])
+    bad[0:4] = struct.pack("<I", 0xDEAD)
+    assert C(hb=ctypes.c_char_p(bytes(bad))) == N.ERR_CORRUPT
+
+
 def test_batch_validation_before_device(lib):
     """Batch calls validate every item on the host before queueing anything."""
     A = 1 << 20
