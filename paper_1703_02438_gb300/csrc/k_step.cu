@@ -23,6 +23,9 @@ namespace nmk {
 
 namespace {
 
+constexpr int K41_WARPS = 16;                    // warps per CTA (each owns whole tiles)
+constexpr int K41_THREADS = K41_WARPS * 32;
+
 struct StepArgs {
   const void* cur;               // the next timestep, n elements of T
   Ctrl* ctrl;                    // the next compression's control block
@@ -53,8 +56,8 @@ __device__ __forceinline__ void step_tiles(const DecodeArgs& A, const StepArgs& 
   const T* cur = static_cast<const T*>(S.cur);
   const unsigned lt = lanemask_lt();
 
-  const long long W = (long long)gridDim.x * K4_WARPS;
-  for (long long gt = (long long)blockIdx.x * K4_WARPS + warp; gt < g.nsub; gt += W) {
+  const long long W = (long long)gridDim.x * K41_WARPS;
+  for (long long gt = (long long)blockIdx.x * K41_WARPS + warp; gt < g.nsub; gt += W) {
     const long long q = gt / g.spb, t = gt - q * g.spb;
     const long long j0 = q * g.epb + t * SUB;
     const long long bend = min((long long)g.n, (long long)((q + 1) * g.epb));
@@ -186,7 +189,7 @@ __device__ __forceinline__ void step_dispatch(const DecodeArgs& A, const StepArg
 }
 
 template <typename T>
-__global__ void __launch_bounds__(K4_THREADS, 2) k41_step(DecodeArgs A, StepArgs S, Consts<T> c) {
+__global__ void __launch_bounds__(K41_THREADS, 2) k41_step(DecodeArgs A, StepArgs S, Consts<T> c) {
   extern __shared__ unsigned int sh[];                           // K1's shared window
   __shared__ __align__(16) unsigned char s_tab[DM_SMEM * 8];     // multipliers m = 1 + centre
   __shared__ __align__(16) numarck_header s_h;
@@ -220,7 +223,7 @@ __global__ void __launch_bounds__(K4_THREADS, 2) k41_step(DecodeArgs A, StepArgs
     const int nm = min(1 << g.B, DM_SMEM);
     T* s_m = reinterpret_cast<T*>(s_tab);
     const T* centres = reinterpret_cast<const T*>(A.blob + g.off_centres);
-    for (int r = threadIdx.x; r < nm; r += K4_THREADS) s_m[r] = t_add((T)1, centres[r]);
+    for (int r = threadIdx.x; r < nm; r += K41_THREADS) s_m[r] = t_add((T)1, centres[r]);
     __syncthreads();
     step_dispatch<T>(A, S, g, s_h.n_inc, s_m, c, h, lmin, lmax);
   }
@@ -238,7 +241,7 @@ cudaError_t launch_step_t(const DecodePlan& D, const CompressPlan& P, cudaStream
     cudaError_t e = cudaFuncSetAttribute(k41_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k41_step<T>, K4_THREADS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k41_step<T>, K41_THREADS, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     if (dev < 64) occ[dev] = per_sm;
@@ -247,7 +250,7 @@ cudaError_t launch_step_t(const DecodePlan& D, const CompressPlan& P, cudaStream
   // when its header was given on the host, else the least it can have)
   long long blocks = (long long)P.sms * per_sm;
   const long long tiles = D.ntiles_hint > 0 ? D.ntiles_hint : (D.count + SUB - 1) / SUB;
-  blocks = std::min(blocks, std::max(1LL, (tiles + K4_WARPS - 1) / K4_WARPS));
+  blocks = std::min(blocks, std::max(1LL, (tiles + K41_WARPS - 1) / K41_WARPS));
   Ctrl* ctrl = reinterpret_cast<Ctrl*>(P.ws + P.wl.ctrl);
   DecodeArgs A{D.blob, D.prev_seg, D.out_seg, D.status, 0, D.count, D.n_expected, &ctrl->error,
                P.g.dtype};
@@ -255,9 +258,9 @@ cudaError_t launch_step_t(const DecodePlan& D, const CompressPlan& P, cudaStream
              reinterpret_cast<unsigned long long*>(P.ws + P.wl.status), P.g.nsub,
              reinterpret_cast<unsigned short*>(P.blob + P.code_off)};
   if constexpr (sizeof(T) == 8)
-    k41_step<double><<<(int)blocks, K4_THREADS, smem, s>>>(A, S, P.cd);
+    k41_step<double><<<(int)blocks, K41_THREADS, smem, s>>>(A, S, P.cd);
   else
-    k41_step<float><<<(int)blocks, K4_THREADS, smem, s>>>(A, S, P.cf);
+    k41_step<float><<<(int)blocks, K41_THREADS, smem, s>>>(A, S, P.cf);
   return cudaGetLastError();
 }
 
