@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="numarck", choices=["numarck", "reference"])
     ap.add_argument("--side", type=int, default=1024, help="grid side (1024 = the full workload)")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 24,
@@ -512,26 +512,30 @@ def run_served(args):
 
 
 def run_e2e(args, xs, n, bound, dist, dev, ws, recon_out=True):
-    """End-to-end metric through the public API: host timesteps in, blobs and reconstructions
-    out, with host<->device copies overlapped with the kernels (see the comment in main)."""
+    """End-to-end metric through the public API: host timesteps in, blobs (and reconstructions)
+    out, each (E, B) chain as in the device-resident run (compress, two chained steps,
+    decompress), with the host<->device copies overlapped with the kernels and with each other.
+
+    Inputs are double-buffered on the device, so the next step's four timesteps are copied in
+    while this step computes; the copies out run on their own streams as soon as each result is
+    ready. The timed region starts before the first timed step's inputs are copied in."""
     import torch
     from paper_1703_02438_gb300 import numarck as N
     nC = len(COMBOS)
     tdt = xs[0].dtype
     L = xs[0].element_size()
     host_x = [xs[t].cpu().pin_memory() for t in range(4)]
-    host_blob = [torch.empty(bound, dtype=torch.uint8).pin_memory() for _ in range(2)]
-    host_rec = [torch.empty(n if recon_out else 1, dtype=tdt).pin_memory()
-                for _ in range(2)]
-    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    host_blob = torch.empty(bound, dtype=torch.uint8).pin_memory()
+    host_rec = torch.empty(n if recon_out else 1, dtype=tdt).pin_memory()
     host_status = torch.zeros(1, dtype=torch.int32).pin_memory()
-    hdrs = [torch.empty(N.HEADER_BYTES, dtype=torch.uint8).pin_memory() for _ in range(2)]
-    xin = [torch.empty(n, dtype=tdt, device=dev) for _ in range(3)]
-    recs = [[torch.empty(n, dtype=tdt, device=dev) for _ in range(2)] for _ in range(nC)]
-    blobs = [torch.empty(bound, dtype=torch.uint8, device=dev) for _ in range(2)]
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    xin = [[torch.empty(n, dtype=tdt, device=dev) for _ in range(4)] for _ in range(2)]
+    NB, NR = 3, 3
+    blobs = [torch.empty(bound, dtype=torch.uint8, device=dev) for _ in range(NB)]
+    recs = [torch.empty(n, dtype=tdt, device=dev) for _ in range(NR)]
+    hdrs = [torch.empty(N.HEADER_BYTES, dtype=torch.uint8).pin_memory() for _ in range(NB)]
     comp = torch.cuda.current_stream()
-    h2d = torch.cuda.Stream()
-    d2h = torch.cuda.Stream()
+    h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
     parts = 4                                         # each large copy is split over 4 streams
     h2d_s = [torch.cuda.Stream() for _ in range(parts)]
     d2h_s = [torch.cuda.Stream() for _ in range(parts)]
@@ -551,83 +555,123 @@ def run_e2e(args, xs, n, bound, dist, dev, ws, recon_out=True):
         for st in streams:
             lead.wait_stream(st)
 
-    def step():
-        loaded, slot_free = {}, [None, None, None]
-        blob_free, rec_free = [None, None], {}
+    def record(stream):
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        return ev
 
-        def load(t):
-            s_ = t % 3
-            if slot_free[s_] is not None:
-                h2d.wait_event(slot_free[s_])
-            split_copy(xin[s_], host_x[t], h2d, h2d_s)
-            ev = torch.cuda.Event()
-            ev.record(h2d)
-            loaded[t] = ev
+    state = {"set_free": [None, None], "blob_free": [None] * NB, "rec_free": [None] * NR,
+             "bi": 0, "ri": 0, "loaded": {}}
+
+    def load(k):
+        """Queue the copy-in of step k's four timesteps into input set k % 2."""
+        st = k % 2
+        if state["set_free"][st] is not None:
+            h2d.wait_event(state["set_free"][st])
+        evs = []
+        for t in range(4):
+            split_copy(xin[st][t], host_x[t], h2d, h2d_s)
+            evs.append(record(h2d))
             tally["h2d"] += n * L
+        state["loaded"][k] = evs
 
-        def flush(pend):
-            k, bi, ev_c, ev_d, c, ri = pend
-            ev_c.synchronize()                       # this pair's header is in pinned memory
-            size = N.blob_size(bytes(hdrs[bi].numpy().tobytes()))
-            d2h.wait_event(ev_c)
-            split_copy(host_blob[bi][:size], blobs[bi][:size], d2h, d2h_s)
-            d2h.wait_event(ev_d)
-            if recon_out:
-                split_copy(host_rec[k % 2], recs[c][ri], d2h, d2h_s)
-            else:                                     # the decode status word only
-                with torch.cuda.stream(d2h):
-                    host_status.copy_(status, non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(d2h)
-            blob_free[bi] = ev
-            rec_free[(c, ri)] = ev
-            tally["d2h"] += size + (n * L if recon_out else 4)
+    pending = []   # (event after the producing call, blob index or None, recon index or None)
 
+    def flush(keep):
+        """Queue the copies out of every pending result but the last `keep`."""
+        while len(pending) > keep:
+            ev, bi, ri = pending.pop(0)
+            d2h.wait_event(ev)
+            if bi is not None:
+                ev.synchronize()                      # the blob's header is in pinned memory
+                size = N.blob_size(bytes(hdrs[bi].numpy().tobytes()))
+                split_copy(host_blob[:size], blobs[bi][:size], d2h, d2h_s)
+                tally["d2h"] += size
+                state["blob_free"][bi] = record(d2h)
+            if ri is not None:
+                if recon_out:
+                    split_copy(host_rec, recs[ri], d2h, d2h_s)
+                    tally["d2h"] += n * L
+                    state["rec_free"][ri] = record(d2h)
+                else:
+                    with torch.cuda.stream(d2h):
+                        host_status.copy_(status, non_blocking=True)
+                    tally["d2h"] += 4
+
+    def new_blob():
+        bi = state["bi"]
+        state["bi"] = (bi + 1) % NB
+        if state["blob_free"][bi] is not None:
+            comp.wait_event(state["blob_free"][bi])
+        return bi
+
+    def new_rec():
+        ri = state["ri"]
+        state["ri"] = (ri + 1) % NR
+        if state["rec_free"][ri] is not None:
+            comp.wait_event(state["rec_free"][ri])
+        return ri
+
+    def produced(bi, ri):
+        if bi is not None:
+            hdrs[bi].copy_(blobs[bi][:N.HEADER_BYTES], non_blocking=True)
+        pending.append((record(comp), bi, ri))
+        flush(1)
+
+    def compute(k):
+        st = k % 2
+        X = xin[st]
+        ld = state["loaded"].pop(k)
+        for c, (E, B) in enumerate(COMBOS):
+            if c == 0:
+                comp.wait_event(ld[0])
+                comp.wait_event(ld[1])
+            b0 = new_blob()
+            N.compress(X[0], X[1], E, B, blob=blobs[b0], workspace=ws, stream=comp)
+            produced(b0, None)
+            if c == 0:
+                comp.wait_event(ld[2])
+            ra, b1 = new_rec(), new_blob()
+            N.decompress_compress(blobs[b0], X[0], X[2], E, B, out=recs[ra], next_blob=blobs[b1],
+                                  workspace=ws, status=status, stream=comp)
+            produced(b1, ra)
+            if c == 0:
+                comp.wait_event(ld[3])
+            rb, b2 = new_rec(), new_blob()
+            N.decompress_compress(blobs[b1], recs[ra], X[3], E, B, out=recs[rb],
+                                  next_blob=blobs[b2], workspace=ws, status=status, stream=comp)
+            produced(b2, rb)
+            rc = new_rec()
+            N.decompress(blobs[b2], recs[rb], out=recs[rc], status=status, stream=comp)
+            produced(None, rc)
+        state["set_free"][st] = record(comp)
+
+    def run(steps):
         load(0)
-        load(1)
-        pending, k = None, 0
-        for t in range(1, 4):
-            if t + 1 <= 3:
-                load(t + 1)
-            comp.wait_event(loaded[t])
-            if t == 1:
-                comp.wait_event(loaded[0])
-            for c, (E, B) in enumerate(COMBOS):
-                prev = xin[0] if t == 1 else recs[c][(t - 1) % 2]
-                bi, ri = k % 2, t % 2
-                if blob_free[bi] is not None:
-                    comp.wait_event(blob_free[bi])
-                if (c, ri) in rec_free:
-                    comp.wait_event(rec_free[(c, ri)])
-                N.compress(prev, xin[t % 3], E, B, blob=blobs[bi], workspace=ws, stream=comp)
-                hdrs[bi].copy_(blobs[bi][:N.HEADER_BYTES], non_blocking=True)
-                ev_c = torch.cuda.Event()
-                ev_c.record(comp)
-                N.decompress(blobs[bi], prev, out=recs[c][ri], status=status, stream=comp)
-                ev_d = torch.cuda.Event()
-                ev_d.record(comp)
-                if pending is not None:
-                    flush(pending)
-                pending = (k, bi, ev_c, ev_d, c, ri)
-                k += 1
-            slot_free[t % 3] = ev_d                   # the last pair of this timestep
-            if t == 1:
-                slot_free[0] = ev_d
-        flush(pending)
+        if steps > 1:
+            load(1)
+        for k in range(steps):
+            compute(k)
+            if k + 2 < steps:
+                load(k + 2)
+        flush(0)
 
-    step()                                            # warm-up (pins pages, loads code)
+    run(1)                                            # warm-up (pins pages, loads code)
     torch.cuda.synchronize()
     tally["h2d"] = tally["d2h"] = 0
     _barrier(dist)
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     a.record(comp)
-    for _ in range(args.e2e_steps):
-        step()
+    h2d.wait_stream(comp)                             # nothing of the timed steps before `a`
+    d2h.wait_stream(comp)
+    run(args.e2e_steps)
     comp.wait_stream(h2d)
     comp.wait_stream(d2h)
     b.record(comp)
     torch.cuda.synchronize()
+    if int(status.item()) != 0:
+        raise RuntimeError(f"device status {int(status.item())} in the end-to-end run")
     e2e_ms = _max_over_ranks(dist, a.elapsed_time(b))
     n_pairs = 3 * nC
     val = _sum_over_ranks(dist, args.e2e_steps * n_pairs * n * L) / (e2e_ms / 1e3) / 1e9
@@ -659,9 +703,9 @@ def run_e2e(args, xs, n, bound, dist, dev, ws, recon_out=True):
         nbytes = 3 * sum(src.numel() * src.element_size() for _, src, _ in pairs_)
         return nbytes / (a.elapsed_time(b) / 1e3) / 1e9
 
-    link = {"d2h_gbs": link_rate([(host_x[0], xin[0], d2h_s)]),
-            "h2d_gbs": link_rate([(xin[1], host_x[1], h2d_s)]),
-            "both_ways_gbs": link_rate([(host_x[0], xin[0], d2h_s), (xin[1], host_x[1], h2d_s)])}
+    link = {"d2h_gbs": link_rate([(host_x[0], xin[0][0], d2h_s)]),
+            "h2d_gbs": link_rate([(xin[0][1], host_x[1], h2d_s)]),
+            "both_ways_gbs": link_rate([(host_x[0], xin[0][0], d2h_s), (xin[0][1], host_x[1], h2d_s)])}
     hb_, db_ = tally["h2d"] / args.e2e_steps, tally["d2h"] / args.e2e_steps
     # E if the step took exactly as long as its copies: each direction at its own rate, and
     # both together at the measured two-way rate
@@ -673,10 +717,11 @@ def run_e2e(args, xs, n, bound, dist, dev, ws, recon_out=True):
            "d2h_bytes_per_step": tally["d2h"] // args.e2e_steps,
            "steps": args.e2e_steps,
            "link": {k: round(v, 1) for k, v in link.items()},
-           "note": ("each timestep copied in once per step; every pair's blob and "
+           "note": ("each timestep copied in once per step (inputs double-buffered: the next "
+                    "step's are copied in while this one computes); every pair's blob and "
                     + ("reconstruction" if recon_out else "decode status word")
-                    + " copied out; copies split over 4 streams each way and overlapped with "
-                      "the kernels")}
+                    + " copied out as soon as it is ready; copies split over 4 streams each way "
+                      "and overlapped with the kernels; chains as in the device-resident run")}
     del host_x, host_blob, host_rec, xin, recs, blobs
     return out
 
@@ -842,9 +887,9 @@ def main():
     one_pass = 2 * L * n + n * Bl / 8 + alpha * n * L      # read p, x once; write the blob once
 
     # end to end through the public API with host buffers, pipelined: each timestep is copied
-    # host->device once per step (pinned, on its own stream, one timestep ahead of the kernels);
+    # host->device once per step (pinned; the next step's inputs while this one computes);
     # every pair's blob (the used bytes, sized from its header) and reconstruction are copied
-    # device->host on a third stream while the next pair computes
+    # device->host on their own streams as soon as they are ready
     e2e = e2e_blob = None
     if not args.no_e2e and args.e2e_steps > 0:
         e2e = run_e2e(args, xs, n, bound, dist, dev, ws)
