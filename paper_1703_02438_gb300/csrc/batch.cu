@@ -191,7 +191,8 @@ int numarck_decompress_batch(const numarck_batch_decode_item* items, int count, 
     if (cudaStreamWaitEvent(P->streams[l], P->fork, 0) != cudaSuccess) return NUMARCK_ERR_CUDA;
   for (int i = 0; i < count; ++i)
     if ((rc = launch_decompress(items[i].blob, items[i].prev, items[i].out, items[i].n,
-                                status_dev, share_sms, P->streams[lane_of[i]])))
+                                status_dev, share_sms, P->streams[lane_of[i]],
+                                std::max(1, lanes / grid_share))))
       return rc;
   for (int l = 0; l < lanes; ++l) {
     if (cudaEventRecord(P->join[l], P->streams[l]) != cudaSuccess) return NUMARCK_ERR_CUDA;

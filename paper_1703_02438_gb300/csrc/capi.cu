@@ -311,7 +311,7 @@ int plan_decompress_check(const void* blob, const void* prev, void* out, int64_t
 }
 
 int launch_decompress(const void* blob, const void* prev, void* out, int64_t n, int32_t* status,
-                      int sms, cudaStream_t s) {
+                      int sms, cudaStream_t s, int concurrency) {
   if (n == 0) return NUMARCK_OK;
   DecodePlan P{};
   P.blob = static_cast<const unsigned char*>(blob);
@@ -323,6 +323,7 @@ int launch_decompress(const void* blob, const void* prev, void* out, int64_t n, 
   P.n_expected = n;
   P.ntiles_hint = 0;
   P.sms = sms;
+  P.concurrency = concurrency;
   trace(0, 2, s);
   if (launch_decode(P, s) != cudaSuccess) return NUMARCK_ERR_CUDA;
   trace(1, 2, s);

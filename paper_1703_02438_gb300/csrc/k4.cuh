@@ -17,6 +17,7 @@ struct DecodeArgs {
   long long start, count, n_expected;
   int* status2;              // a second error word (the next compression's), or null
   int dtype;                 // NUMARCK_F32 / NUMARCK_F64 the blob must hold, or 0 for either
+  int seg_log2;              // each sub-block is decoded by 2^seg_log2 warps (see seg_count)
 };
 
 // An error found on the device goes to both status words (either may be null).
@@ -97,6 +98,39 @@ __device__ __forceinline__ typename Field<B>::type load_field(const unsigned* tw
       return (F)(v >> o);
     }
   }
+}
+
+
+// Warps per sub-block. A warp decodes its part of a sub-block in 128-point steps, each one a
+// dependent round trip to memory (the fields and prev, then the incompressible values), so with
+// few sub-blocks (small variables) one warp per sub-block leaves most of the GPU idle and runs a
+// 32-step chain. Splitting a sub-block into 2^seg_log2 segments gives each warp 32 >> seg_log2
+// steps; a warp that starts inside a sub-block first counts the markers before its segment
+// (markers_before: loads that do not depend on each other), which is where its incompressible
+// values start. Chosen so that the units (sub-block segments) fill the resident warps.
+__host__ __forceinline__ int seg_log2_for(long long tiles, long long resident_warps) {
+  int s = 0;
+  while (s < 3 && (tiles << s) < resident_warps) ++s;
+  return s;
+}
+
+// Number of incompressible points (fields equal to the marker M) among the first e_end points
+// of a sub-block (e_end a multiple of K4_SEG, at most its point count cnt); warp-uniform.
+template <int B>
+__device__ __forceinline__ unsigned markers_before(const unsigned* tw, int twords, int cnt,
+                                                   int e_end, int lane) {
+  constexpr int FB = 4 * B;
+  constexpr unsigned M = (1u << B) - 1u;
+  unsigned c = 0;
+#pragma unroll 4
+  for (int s0 = 0; s0 < e_end; s0 += K4_SEG) {
+    const typename Field<B>::type field = load_field<B>(tw, twords, (s0 / K4_SEG) * FB, lane);
+    const int e0 = s0 + 4 * lane;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      c += (e0 + k < cnt && ((unsigned)(field >> (k * B)) & M) == M) ? 1u : 0u;
+  }
+  return __reduce_add_sync(0xffffffffu, c);
 }
 
 }  // namespace nmk

@@ -17,6 +17,8 @@
 // The kernel reads the blob header from device memory and validates it (magic, version, status
 // word, geometry implied by n/B/block size, counts), so decompression needs no host round trip
 // after compression: a compress -> decompress chain stays asynchronous on one stream.
+#include <algorithm>
+
 #include "k4.cuh"
 
 namespace nmk {
@@ -44,7 +46,12 @@ __device__ __forceinline__ void decode_tiles(const DecodeArgs& A, const Geometry
 
   const long long seg_lo = A.start, seg_hi = A.start + A.count;
   const long long W = (long long)gridDim.x * K4_WARPS;
-  for (long long gt = g0 + (long long)blockIdx.x * K4_WARPS + warp; gt <= g1; gt += W) {
+  const int sl = A.seg_log2;                     // units: 2^sl segments per sub-block
+  const int seglen = SUB >> sl;
+  const long long u1 = (g1 + 1) << sl;
+  for (long long u = (g0 << sl) + (long long)blockIdx.x * K4_WARPS + warp; u < u1; u += W) {
+    const long long gt = u >> sl;
+    const int sbeg = (int)(u & ((1 << sl) - 1)) * seglen;
     const long long q = gt / g.spb, t = gt - q * g.spb;
     const long long j0 = q * g.epb + t * SUB;
     const long long bend = min((long long)g.n, (long long)((q + 1) * g.epb));
@@ -59,22 +66,25 @@ __device__ __forceinline__ void decode_tiles(const DecodeArgs& A, const Geometry
       continue;
     }
     const unsigned* tw = reinterpret_cast<const unsigned*>(index + tstart);
-    // elements [e_lo, e_hi) of the tile lie in the segment; pt/ot address tile element 0
+    // elements [e_lo, e_hi) of the tile lie in the requested range; pt/ot address tile element 0
     const int e_lo = (int)max(0LL, seg_lo - j0);
     const int e_hi = (int)min((long long)cnt, seg_hi - j0);
+    // this warp's steps: [sbeg, send) of the tile, up to e_hi
+    const int send = min(min(cnt, sbeg + seglen), e_hi);
+    if (sbeg >= send || sbeg + seglen <= e_lo) continue;
     const T* pt = prev + (j0 - seg_lo);
     T* ot = out + (j0 - seg_lo);
     const bool vec = e_lo == 0 && ((reinterpret_cast<uintptr_t>(pt) |
                                     reinterpret_cast<uintptr_t>(ot)) & 15) == 0;
-    long long run = base;
-    for (int s0 = 0; s0 < e_hi; s0 += K4_SEG * k4_unroll<T>()) {
+    long long run = base + (sbeg ? markers_before<B>(tw, twords, cnt, sbeg, lane) : 0u);
+    for (int s0 = sbeg; s0 < send; s0 += K4_SEG * k4_unroll<T>()) {
       F field[k4_unroll<T>()];
       T pv[k4_unroll<T>()][4];
 #pragma unroll
       for (int u = 0; u < k4_unroll<T>(); ++u) {
         const int sb0 = s0 + u * K4_SEG;
         const int e0 = sb0 + 4 * lane;
-        field[u] = sb0 < e_hi ? load_field<B>(tw, twords, (sb0 / K4_SEG) * FB, lane) : (F)0;
+        field[u] = sb0 < send ? load_field<B>(tw, twords, (sb0 / K4_SEG) * FB, lane) : (F)0;
         if (vec && sb0 + K4_SEG <= e_hi) {
           ld4(pt + e0, pv[u]);
         } else {
@@ -86,7 +96,7 @@ __device__ __forceinline__ void decode_tiles(const DecodeArgs& A, const Geometry
 #pragma unroll
       for (int u = 0; u < k4_unroll<T>(); ++u) {
         const int sb0 = s0 + u * K4_SEG;
-        if (sb0 >= e_hi) break;                  // uniform across the warp
+        if (sb0 >= send) break;                  // uniform across the warp
         const int e0 = sb0 + 4 * lane;
         unsigned id[4];
         unsigned nib = 0;
@@ -131,7 +141,7 @@ __device__ __forceinline__ void decode_tiles(const DecodeArgs& A, const Geometry
         }
       }
     }
-    if (e_hi == cnt && lane == 0) {
+    if (send == cnt && lane == 0) {             // this warp ends the tile: all its markers seen
       const long long next = (gt + 1 < g.nsub) ? sub_off[gt + 1] : n_inc;
       if (run != next) report(A, NUMARCK_ERR_CORRUPT);
     }
@@ -176,7 +186,7 @@ __global__ void __launch_bounds__(K4_THREADS, 2) k4_decode(DecodeArgs A) {
       g1 = q1 * g.spb + (last - q1 * g.epb) / SUB;
     }
     if (rc && blockIdx.x == 0) report(A, rc);
-    s_ok = rc == 0 && g1 >= g0 + (long long)blockIdx.x * K4_WARPS;
+    s_ok = rc == 0 && ((g1 - g0 + 1) << A.seg_log2) > (long long)blockIdx.x * K4_WARPS;
     s_g = g;
     s_g0 = g0;
     s_g1 = g1;
@@ -215,12 +225,16 @@ cudaError_t launch_decode(const DecodePlan& P, cudaStream_t s) {
     if (dev < 64) occ[dev] = per_sm;
   }
   long long blocks = (long long)P.sms * per_sm;
+  // sub-blocks touched (exact with a host header; else the fewest the range can touch)
+  const long long tiles = P.ntiles_hint > 0 ? P.ntiles_hint : (P.count + SUB - 1) / SUB;
+  // (with `concurrency` decodes sharing the GPU, each can count on its share of the warps)
+  const int sl = seg_log2_for(tiles, blocks * K4_WARPS / std::max(1, P.concurrency));
   if (P.ntiles_hint > 0) {
-    const long long need = (P.ntiles_hint + K4_WARPS - 1) / K4_WARPS;
+    const long long need = ((P.ntiles_hint << sl) + K4_WARPS - 1) / K4_WARPS;
     if (blocks > need) blocks = need;
   }
   DecodeArgs A{P.blob, P.prev_seg, P.out_seg, P.status, P.start, P.count, P.n_expected, P.status2,
-               P.dtype};
+               P.dtype, sl};
   k4_decode<<<(int)blocks, K4_THREADS, 0, s>>>(A);
   return cudaGetLastError();
 }

@@ -57,7 +57,12 @@ __device__ __forceinline__ void step_tiles(const DecodeArgs& A, const StepArgs& 
   const unsigned lt = lanemask_lt();
 
   const long long W = (long long)gridDim.x * K41_WARPS;
-  for (long long gt = (long long)blockIdx.x * K41_WARPS + warp; gt < g.nsub; gt += W) {
+  const int sl = A.seg_log2;                     // units: 2^sl segments per sub-block
+  const int seglen = SUB >> sl;
+  const long long u1 = g.nsub << sl;
+  for (long long u = (long long)blockIdx.x * K41_WARPS + warp; u < u1; u += W) {
+    const long long gt = u >> sl;
+    const int sbeg = (int)(u & ((1 << sl) - 1)) * seglen;
     const long long q = gt / g.spb, t = gt - q * g.spb;
     const long long j0 = q * g.epb + t * SUB;
     const long long bend = min((long long)g.n, (long long)((q + 1) * g.epb));
@@ -72,6 +77,8 @@ __device__ __forceinline__ void step_tiles(const DecodeArgs& A, const StepArgs& 
       continue;
     }
     const unsigned* tw = reinterpret_cast<const unsigned*>(index + tstart);
+    const int send = min(cnt, sbeg + seglen);      // this warp's points [sbeg, send) of the tile
+    if (sbeg >= send) continue;
     const T* pt = prev + j0;
     T* ot = out + j0;
     const T* xt = cur + j0;
@@ -79,8 +86,8 @@ __device__ __forceinline__ void step_tiles(const DecodeArgs& A, const StepArgs& 
     const bool vec = ((reinterpret_cast<uintptr_t>(pt) | reinterpret_cast<uintptr_t>(ot) |
                        reinterpret_cast<uintptr_t>(xt)) & 15) == 0;
     const bool cvec = (reinterpret_cast<uintptr_t>(ct) & 7) == 0;
-    long long run = base;
-    for (int s0 = 0; s0 < cnt; s0 += K4_SEG) {
+    long long run = base + (sbeg ? markers_before<B>(tw, twords, cnt, sbeg, lane) : 0u);
+    for (int s0 = sbeg; s0 < send; s0 += K4_SEG) {
       const int e0 = s0 + 4 * lane;
       const bool whole = s0 + K4_SEG <= cnt;     // uniform across the warp
       const F field = load_field<B>(tw, twords, (s0 / K4_SEG) * FB, lane);
@@ -168,7 +175,7 @@ __device__ __forceinline__ void step_tiles(const DecodeArgs& A, const StepArgs& 
         hist_add(h, binned, b, lmin, lmax);
       }
     }
-    if (lane == 0) {
+    if (send == cnt && lane == 0) {             // this warp ends the tile: all its markers seen
       const long long next = (gt + 1 < g.nsub) ? sub_off[gt + 1] : n_inc;
       if (run != next) report(A, NUMARCK_ERR_CORRUPT);
     }
@@ -250,10 +257,11 @@ cudaError_t launch_step_t(const DecodePlan& D, const CompressPlan& P, cudaStream
   // when its header was given on the host, else the least it can have)
   long long blocks = (long long)P.sms * per_sm;
   const long long tiles = D.ntiles_hint > 0 ? D.ntiles_hint : (D.count + SUB - 1) / SUB;
-  blocks = std::min(blocks, std::max(1LL, (tiles + K41_WARPS - 1) / K41_WARPS));
+  const int sl = seg_log2_for(tiles, blocks * K41_WARPS);
+  blocks = std::min(blocks, std::max(1LL, ((tiles << sl) + K41_WARPS - 1) / K41_WARPS));
   Ctrl* ctrl = reinterpret_cast<Ctrl*>(P.ws + P.wl.ctrl);
   DecodeArgs A{D.blob, D.prev_seg, D.out_seg, D.status, 0, D.count, D.n_expected, &ctrl->error,
-               P.g.dtype};
+               P.g.dtype, sl};
   StepArgs S{P.cur, ctrl, reinterpret_cast<unsigned long long*>(P.ws + P.wl.hist),
              reinterpret_cast<unsigned long long*>(P.ws + P.wl.status), P.g.nsub,
              reinterpret_cast<unsigned short*>(P.blob + P.code_off)};

@@ -35,6 +35,7 @@ struct DecodePlan {
   int sms;
   int* status2;            // optional second error word (the next compression's Ctrl::error)
   int dtype;               // element type the blob must hold (0: either)
+  int concurrency;         // decodes expected to share the GPU with this one (0 or 1: none)
 };
 
 cudaError_t launch_anchor_min(const CompressPlan& P, cudaStream_t s);  // K0 (ANCHOR_MIN only)
@@ -65,7 +66,7 @@ int launch_compress(const CompressPlan& P, cudaStream_t s);
 int launch_compress_tail(const CompressPlan& P, cudaStream_t s);   // everything after K1
 int plan_decompress_check(const void* blob, const void* prev, void* out, int64_t n);
 int launch_decompress(const void* blob, const void* prev, void* out, int64_t n, int32_t* status,
-                      int sms, cudaStream_t s);
+                      int sms, cudaStream_t s, int concurrency = 1);
 int current_device_sms();
 
 }  // namespace nmk
