@@ -16,8 +16,7 @@ round-to-nearest-even, so no multiply-add is fused and the order of operations i
 the order written here. Library primitives used as steps: np.unique / np.bincount (counting),
 np.lexsort / np.sort (ordering), np.packbits (bit order), np.searchsorted (lookup).
 
-Readings of the paper where it is silent, ambiguous or garbled (each is used below and
-listed in DESIGN.md):
+Readings of the paper where it is silent, ambiguous or garbled (each is used below):
   R1  a ratio that is not finite (prev = 0, non-finite inputs) is not binnable: the point
       is incompressible. A ratio with |ratio| > cap = 2^21 * 2E is not binnable either
       (it keeps every bin id inside a 2^22-bin window).

@@ -23,8 +23,6 @@ constexpr int WIN_LOG2 = NUMARCK_WINDOW_LOG2;   // |ratio| <= 2^21 * w
 constexpr int HWIN = (1 << (WIN_LOG2 + 1)) + 16; // global histogram window (bins)
 constexpr int HMARGIN = 8;                      // spare bins at each end of the window
 constexpr int SH_BINS = 16384;                  // K1 shared-memory histogram window
-constexpr int RW_BINS = 8192;                   // K3 shared-memory rank window
-constexpr int MT_SMEM = 1024;                   // K3 multipliers kept in shared memory
 constexpr int DM_SMEM = 4096;                   // K4 multipliers kept in shared memory
 constexpr int TILE_THREADS = 512;               // K3/K4 block size
 constexpr int EPT = SUB / TILE_THREADS;         // elements per thread per tile (8)
