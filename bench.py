@@ -42,6 +42,15 @@ COMBOS = [(1e-3, 8), (1e-3, 10), (1e-4, 8), (1e-4, 10)]
 METRIC = "compress+decompress input GB/s (and % of HBM peak) on 1 GB300, bit-exact vs oracle"
 WORKLOAD = ("FLASH-like 3-D float64 field 1024^3 (8 GiB/step), 4 timesteps, 3 closed-loop pairs "
             "x E{1e-3,1e-4} x B{8,10}")
+
+
+def workload_label(side: int, f32: bool) -> str:
+    """The workload string of a run (the headline workload is side 1024, float64)."""
+    L = 4 if f32 else 8
+    gib = side ** 3 * L / 2 ** 30
+    size = f"{gib:.0f} GiB" if gib >= 1 else f"{side ** 3 * L / 2 ** 20:.0f} MiB"
+    return (f"FLASH-like 3-D {'float32 (cast)' if f32 else 'float64'} field {side}^3 "
+            f"({size}/step), 4 timesteps, 3 closed-loop pairs x E{{1e-3,1e-4}} x B{{8,10}}")
 KERNEL_FILES = {"k3_assign": ["k_assign.cu", "common.cuh"],
                 "k3_exact": ["k_assign.cu", "common.cuh"],
                 "k1_hist": ["k_hist.cu", "k1.cuh", "common.cuh"],
@@ -972,6 +981,41 @@ def main():
     comp_alg = alg["k1_hist"] + alg["k3_assign"] + alg["k3_exact"]
     one_pass = 2 * L * n + n * Bl / 8 + alpha * n * L      # read p, x once; write the blob once
 
+    # quality of every pair of the step, from one more run of each chain (outside the timed
+    # region): CR (Eq. 2, raw blob), ME (Eq. 3), the largest relative error, and the points
+    # whose reconstruction fails |R - x| <= E|x| evaluated in T (none may: markers are exact
+    # and every indexed point passed that check when it was compressed)
+    quality = []
+    for E, B in combos:
+        row = {"E": E, "B": B, "CR": [], "ME": [], "max_rel_err": [], "alpha": [],
+               "bound_violations": 0}
+        N.compress(xs[0], xs[1], E, B, blob=blobs[0], workspace=ws)
+        prev = xs[0]
+        for t in range(1, 4):
+            if t < 3:
+                rec, _ = N.decompress_compress(blobs[(t - 1) % 2], prev, xs[t + 1], E, B,
+                                               out=recon[t % 2], next_blob=blobs[t % 2],
+                                               workspace=ws, status=status)
+            else:
+                rec = N.decompress(blobs[(t - 1) % 2], prev, out=recon[t % 2], status=status)
+            h = N.parse_header(N.header_bytes(blobs[(t - 1) % 2]))
+            x = xs[t]
+            xd, rd = x.double(), rec.double()
+            nz = xd != 0
+            rel = torch.where(nz, (xd - rd).abs_().div_(xd.abs()), torch.zeros((), dtype=torch.float64,
+                                                                            device=dev))
+            row["CR"].append(n * L / h["total_bytes"])
+            row["ME"].append(float(rel.sum().item()) / max(1, int(nz.sum().item())))
+            row["max_rel_err"].append(float(rel.max().item()))
+            row["alpha"].append(h["n_inc"] / n)
+            row["bound_violations"] += int(((rec - x).abs_() > x.abs().mul_(E)).sum().item())
+            del xd, rd, nz, rel
+            prev = rec
+        quality.append(row)
+    torch.cuda.synchronize()
+    if int(status.item()) != 0:
+        raise RuntimeError(f"device status {int(status.item())} in the quality run")
+
     # end to end through the public API with host buffers, pipelined: each timestep is copied
     # host->device once per step (pinned; the next step's inputs while this one computes);
     # every pair's blob (the used bytes, sized from its header) and reconstruction are copied
@@ -996,11 +1040,11 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.f32 else "f64",
             "data": "synthetic",
-            "config": {"workload": (WORKLOAD.replace("float64", "float32 (cast)").replace(
-                           "8 GiB/step", "4 GiB/step") if args.f32 else WORKLOAD),
+            "config": {"workload": workload_label(side, args.f32),
                        "n": n, "pairs_per_step": n_pairs,
-                       "chained": not args.no_fuse,
-                       "l2": "inputs 8 GiB per array >> 129 MB L2: no flush",
+                       "chained": not args.no_fuse, "seed": synth.seed_for(1, rank),
+                       "l2": (f"inputs {n * L / 2 ** 30:.2f} GiB per array > 129 MB L2: no flush"
+                              if n * L > 129e6 else "inputs fit in L2: warm-cache figure"),
                        "parallelism": f"replicas x{world} (independent series per GPU)"},
             "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
@@ -1013,6 +1057,9 @@ def main():
             "compress_one_pass_frac": one_pass / (t_comp / 1e3) / 1e9 / peak,
             "decompress_gbs": n * L / (avg["k4_decode"] / 1e3) / 1e9,
             "alpha_last": alpha, "B_last": Bl, "auto_b": bool(args.auto_b),
+            "quality": {"per_chain": quality,
+                        "max_rel_err_over_E": max(max(r["max_rel_err"]) / r["E"] for r in quality),
+                        "bound_violations": sum(r["bound_violations"] for r in quality)},
             "clocks": clk, "e2e": e2e, "e2e_blobs_only": e2e_blob, "cpu_baseline": cpu,
             "gpu_launches": args.steps * len(COMBOS) * ((21 if args.no_fuse else 19)
                                                         + (3 if args.auto_b else 0)),

@@ -122,6 +122,7 @@ size_t numarck_batch_workspace_bytes(const numarck_batch_item* items, int count,
 
 int numarck_compress_batch(const numarck_batch_item* items, int count, int lanes, int grid_share,
                            void* ws, size_t ws_bytes, numarck_stream_t stream) {
+  nmk::NvtxRange nvtx_("numarck_compress_batch");
   if (!items || count < 0 || grid_share < 1) return NUMARCK_ERR_INVALID_ARG;
   if (count == 0) return NUMARCK_OK;
   lanes = clamp_lanes(lanes, count);
@@ -166,6 +167,7 @@ int numarck_compress_batch(const numarck_batch_item* items, int count, int lanes
 
 int numarck_decompress_batch(const numarck_batch_decode_item* items, int count, int lanes,
                              int grid_share, int32_t* status_dev, numarck_stream_t stream) {
+  nmk::NvtxRange nvtx_("numarck_decompress_batch");
   if (!items || count < 0 || grid_share < 1) return NUMARCK_ERR_INVALID_ARG;
   if (count == 0) return NUMARCK_OK;
   lanes = clamp_lanes(lanes, count);

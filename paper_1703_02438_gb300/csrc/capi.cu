@@ -337,6 +337,7 @@ extern "C" {
 int numarck_compress(const void* prev, const void* cur, int64_t n, const numarck_params* p,
                      void* blob, size_t blob_cap, void* ws, size_t ws_bytes,
                      numarck_stream_t stream) {
+  nmk::NvtxRange nvtx_("numarck_compress");
   CompressPlan P;
   const int rc = plan_compress(prev, cur, n, p, blob, blob_cap, ws, ws_bytes, &P);
   if (rc) return rc;
@@ -371,6 +372,7 @@ int numarck_blob_size(const void* header_host, size_t* bytes) {
 
 int numarck_decompress(const void* blob, const void* header_host, const void* prev, void* out,
                        int64_t n, int32_t* status_dev, numarck_stream_t stream) {
+  nmk::NvtxRange nvtx_("numarck_decompress");
   if (n < 0) return NUMARCK_ERR_INVALID_ARG;
   return decode(blob, header_host, prev, 0, n, out, n, status_dev, stream);
 }
@@ -378,6 +380,7 @@ int numarck_decompress(const void* blob, const void* header_host, const void* pr
 int numarck_decompress_range(const void* blob, const void* header_host, const void* prev_seg,
                              int64_t start, int64_t count, void* out_seg, int32_t* status_dev,
                              numarck_stream_t stream) {
+  nmk::NvtxRange nvtx_("numarck_decompress_range");
   return decode(blob, header_host, prev_seg, start, count, out_seg, -1, status_dev, stream);
 }
 
@@ -385,6 +388,7 @@ int numarck_decompress_compress(const void* blob, const void* header_host, const
                                 void* out, int64_t n, int32_t* status_dev, const void* next_cur,
                                 const numarck_params* p, void* next_blob, size_t next_blob_cap,
                                 void* ws, size_t ws_bytes, numarck_stream_t stream) {
+  nmk::NvtxRange nvtx_("numarck_decompress_compress");
   if (n < 0) return NUMARCK_ERR_INVALID_ARG;
   int rc = plan_decompress_check(blob, prev, out, n);
   if (rc) return rc;
@@ -474,6 +478,7 @@ size_t numarck_zindex_workspace_bytes(const void* header_host) {
 
 int numarck_deflate_index(const void* blob, const void* header_host, void* zindex, size_t zcap,
                           void* ws, size_t ws_bytes, numarck_stream_t stream) {
+  nmk::NvtxRange nvtx_("numarck_deflate_index");
   Geometry g;
   int rc = blob_geometry(header_host, &g);
   if (rc) return rc;
@@ -507,6 +512,7 @@ int numarck_deflate_index(const void* blob, const void* header_host, void* zinde
 int numarck_inflate_index(const void* zindex, size_t zbytes, const void* header_host, void* blob,
                           int64_t start, int64_t count, int32_t* status_dev,
                           numarck_stream_t stream) {
+  nmk::NvtxRange nvtx_("numarck_inflate_index");
   Geometry g;
   int rc = blob_geometry(header_host, &g);
   if (rc) return rc;

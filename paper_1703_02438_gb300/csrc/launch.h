@@ -1,9 +1,20 @@
 // launch.h — host-side launchers of the NUMARCK kernels (one translation unit per kernel family).
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 
 namespace nmk {
+
+// An NVTX range around one entry point (header-only NVTX 3: free unless a profiler is attached),
+// so that traces group each call's kernels under its name.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Everything a compression launch needs; built and validated by the C ABI (capi.cu).
 struct CompressPlan {

@@ -26,6 +26,7 @@ bool g_dirty[kMaxDevices] = {false};
 extern "C" int numarck_compress_noalloc(const void* prev, const void* cur, int64_t n,
                                         const numarck_params* p, void* blob, size_t blob_cap,
                                         numarck_stream_t stream) {
+  nmk::NvtxRange nvtx_("numarck_compress_noalloc");
   const size_t need = numarck_workspace_bytes(n, p);
   if (need == 0) return NUMARCK_ERR_INVALID_ARG;
   if (need > (size_t)NUMARCK_NOALLOC_SCRATCH_BYTES) return NUMARCK_ERR_CAPACITY;
