@@ -981,6 +981,17 @@ def main():
     comp_alg = alg["k1_hist"] + alg["k3_assign"] + alg["k3_exact"]
     one_pass = 2 * L * n + n * Bl / 8 + alpha * n * L      # read p, x once; write the blob once
 
+    # end to end through the public API with host buffers, pipelined: each timestep is copied
+    # host->device once per step (pinned; the next step's inputs while this one computes);
+    # every pair's blob (the used bytes, sized from its header) and reconstruction are copied
+    # device->host on their own streams as soon as they are ready
+    e2e = e2e_blob = None
+    if not args.no_e2e and args.e2e_steps > 0:
+        e2e = run_e2e(args, xs, n, bound, dist, dev, ws)
+        # the same without the reconstruction leaving the device (it is the next prev of the
+        # closed loop, Eq. 4): the blobs and the decode status are the step's results
+        e2e_blob = run_e2e(args, xs, n, bound, dist, dev, ws, recon_out=False)
+
     # quality of every pair of the step, from one more run of each chain (outside the timed
     # region): CR (Eq. 2, raw blob), ME (Eq. 3), the largest relative error, and the points
     # whose reconstruction fails |R - x| <= E|x| evaluated in T (none may: markers are exact
@@ -1015,17 +1026,6 @@ def main():
     torch.cuda.synchronize()
     if int(status.item()) != 0:
         raise RuntimeError(f"device status {int(status.item())} in the quality run")
-
-    # end to end through the public API with host buffers, pipelined: each timestep is copied
-    # host->device once per step (pinned; the next step's inputs while this one computes);
-    # every pair's blob (the used bytes, sized from its header) and reconstruction are copied
-    # device->host on their own streams as soon as they are ready
-    e2e = e2e_blob = None
-    if not args.no_e2e and args.e2e_steps > 0:
-        e2e = run_e2e(args, xs, n, bound, dist, dev, ws)
-        # the same without the reconstruction leaving the device (it is the next prev of the
-        # closed loop, Eq. 4): the blobs and the decode status are the step's results
-        e2e_blob = run_e2e(args, xs, n, bound, dist, dev, ws, recon_out=False)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
