@@ -216,6 +216,131 @@ __device__ __forceinline__ void anchor_consts(Consts<T>& c, const Geometry& g, c
   }
 }
 
+
+// Codes e0 .. e0+15 of a tile (tile-relative) as eight words of two codes (the lower first), for
+// a lane whose 16 points all lie in the tile. The tile's codes start `sh` codes into the
+// 16-byte-aligned word `wb` of the codes array; a0, a1 are this lane's two aligned 16-byte words
+// (codes wb+e0 .. wb+e0+15) and b0 the next 16 bytes (the next lane's a0).
+__device__ __forceinline__ void shifted_codes(const uint4& a0, const uint4& a1, const uint4& b0,
+                                              int sh, unsigned (&cw)[8]) {
+  const unsigned win[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w,
+                            b0.x, b0.y, b0.z, b0.w};
+  const bool odd = sh & 1;
+  switch (sh >> 1) {                             // uniform across the warp
+#define NMK_SHIFT_CASE(Q)                                                                     \
+  case Q:                                                                                     \
+    _Pragma("unroll") for (int i = 0; i < 8; ++i)                                             \
+      cw[i] = odd ? __funnelshift_r(win[i + Q], win[i + Q + 1], 16) : win[i + Q];              \
+    break;
+    NMK_SHIFT_CASE(0)
+    NMK_SHIFT_CASE(1)
+    NMK_SHIFT_CASE(2)
+    NMK_SHIFT_CASE(3)
+#undef NMK_SHIFT_CASE
+  }
+}
+
+// K3a's tile loop for even B: 512-point steps in which lane l holds points 16l .. 16l+15, so that
+// its sixteen B-bit indices fill B/2 whole 32-bit words of the step's image (LSB first) and its
+// sixteen incompressible flags one 16-bit half-ballot word: the lane stores both itself, without
+// shuffles. Codes arrive as two 16-byte loads per lane (a tile that starts off a 16-byte boundary
+// funnel-shifts each lane's words with the next lane's). Lanes past the tile end, or whose codes
+// would reach past the codes array, read their codes one by one.
+template <int B, typename T>
+__device__ __forceinline__ void k3a_tiles_even(const AssignArgs<T>& A,
+                                               const unsigned short* s_tab, long long W, int lane,
+                                               int tid, int any) {
+  constexpr unsigned M = (1u << B) - 1u;
+  constexpr bool kSentinel = B < 16;             // see k3_assign
+  constexpr int EL = 16, WL = B / 2, SEGW = 32 * EL;
+  const Geometry& g = A.g;
+  for (long long gt = (long long)blockIdx.x * K3_WARPS + (tid >> 5); gt < g.nsub; gt += W) {
+    const TileRef tr = tile_ref<B>(g, gt, A.blob, A.codes);
+    const int cnt = tr.cnt;
+    const int sh = (int)(tr.j0 & 7);
+    const long long wb = tr.j0 - sh;             // 16-byte-aligned code index at or before j0
+    const unsigned short* ct = A.codes + tr.j0;
+    const uint4* cw4 = reinterpret_cast<const uint4*>(A.codes + wb);
+    int count = 0;
+    unsigned far = 0;
+    for (int sb0 = 0; sb0 < cnt; sb0 += SEGW) {
+      const int e0 = sb0 + EL * lane;
+      unsigned cw[8];
+      const long long w0 = wb + e0;              // this lane's first aligned code
+      uint4 a0 = make_uint4(0u, 0u, 0u, 0u), a1 = a0;
+      if (w0 + 8 <= g.n) a0 = __ldcs(cw4 + (e0 >> 3));
+      if (w0 + 16 <= g.n) a1 = __ldcs(cw4 + (e0 >> 3) + 1);
+      uint4 b0;
+      b0.x = __shfl_down_sync(0xffffffffu, a0.x, 1);
+      b0.y = __shfl_down_sync(0xffffffffu, a0.y, 1);
+      b0.z = __shfl_down_sync(0xffffffffu, a0.z, 1);
+      b0.w = __shfl_down_sync(0xffffffffu, a0.w, 1);
+      const bool inside = e0 + EL <= cnt;
+      if (lane == 31 && sh && inside && w0 + 24 <= g.n) b0 = __ldcs(cw4 + (e0 >> 3) + 2);
+      if (inside && (sh == 0 || w0 + 24 <= g.n)) {
+        if (sh == 0) {
+          cw[0] = a0.x; cw[1] = a0.y; cw[2] = a0.z; cw[3] = a0.w;
+          cw[4] = a1.x; cw[5] = a1.y; cw[6] = a1.z; cw[7] = a1.w;
+        } else {
+          shifted_codes(a0, a1, b0, sh, cw);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const unsigned lo = e0 + 2 * i < cnt ? (unsigned)ct[e0 + 2 * i] : CODE_NONE;
+          const unsigned hi = e0 + 2 * i + 1 < cnt ? (unsigned)ct[e0 + 2 * i + 1] : CODE_NONE;
+          cw[i] = lo | (hi << 16);
+        }
+      }
+      __syncwarp();                              // every lane holds its codes before any flag store
+      unsigned w[WL];
+#pragma unroll
+      for (int i = 0; i < WL; ++i) w[i] = 0u;
+      unsigned fl = 0;
+#pragma unroll
+      for (int k = 0; k < EL; ++k) {
+        const unsigned code = (cw[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
+        const unsigned r = s_tab[code];
+        unsigned idx;
+        if constexpr (kSentinel) {
+          far = max(far, r);
+          idx = min(r, M);
+        } else {
+          far |= code == CODE_FAR ? 1u : 0u;
+          idx = r;
+        }
+        const bool in = e0 + k < cnt;
+        fl |= (in && idx == M) ? (1u << k) : 0u;
+        idx = in ? idx : 0u;                     // zero fields past the tile end
+        const int bit = k * B;
+        w[bit >> 5] |= idx << (bit & 31);
+        if ((bit & 31) + B > 32) w[(bit >> 5) + 1] |= idx >> (32 - (bit & 31));
+      }
+      if (e0 < cnt) tr.halves[e0 >> 4] = (unsigned short)fl;
+      count += __popc(fl);
+      const int ow = (sb0 / SEGW) * (32 * WL) + lane * WL;   // first word of the lane's fields
+      if (ow < tr.twords) {
+        if constexpr (WL % 4 == 0) {
+#pragma unroll
+          for (int i = 0; i < WL; i += 4)
+            *reinterpret_cast<uint4*>(tr.tw + ow + i) = make_uint4(w[i], w[i + 1], w[i + 2], w[i + 3]);
+        } else if constexpr (WL % 2 == 0) {
+#pragma unroll
+          for (int i = 0; i < WL; i += 2)
+            if (ow + i < tr.twords) *reinterpret_cast<uint2*>(tr.tw + ow + i) = make_uint2(w[i], w[i + 1]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < WL; ++i)
+            if (ow + i < tr.twords) tr.tw[ow + i] = w[i];
+        }
+      }
+    }
+    count = __reduce_add_sync(0xffffffffu, count);
+    const bool fix = any && __any_sync(0xffffffffu, kSentinel ? far > M : far != 0u);
+    if (lane == 0) A.tstatus[gt] = (unsigned long long)count | (fix ? K3_FAR_FLAG : 0ull);
+  }
+}
+
 template <typename T, int B>
 __global__ void __launch_bounds__(K3_THREADS, 1) k3_assign(AssignArgs<T> A) {
   constexpr unsigned M = (1u << B) - 1u;
@@ -244,6 +369,9 @@ __global__ void __launch_bounds__(K3_THREADS, 1) k3_assign(AssignArgs<T> A) {
   __syncthreads();   // the only block-wide barriers: the table is read-only from here on
 
   const long long W = (long long)gridDim.x * K3_WARPS;
+  if constexpr (B % 2 == 0) {
+    k3a_tiles_even<B>(A, s_tab, W, lane, tid, any);
+  } else {
   for (long long gt = (long long)blockIdx.x * K3_WARPS + (tid >> 5); gt < g.nsub; gt += W) {
     const TileRef tr = tile_ref<B>(g, gt, A.blob, A.codes);
     const int cnt = tr.cnt;
@@ -318,6 +446,7 @@ __global__ void __launch_bounds__(K3_THREADS, 1) k3_assign(AssignArgs<T> A) {
     count = __reduce_add_sync(0xffffffffu, count);
     const bool fix = any && __any_sync(0xffffffffu, kSentinel ? far > M : far != 0u);
     if (lane == 0) A.tstatus[gt] = (unsigned long long)count | (fix ? K3_FAR_FLAG : 0ull);
+  }
   }
 }
 
