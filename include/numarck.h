@@ -366,6 +366,19 @@ int numarck_decompress_batch(const numarck_batch_decode_item* items, int count, 
  * Returns NUMARCK_ERR_INVALID_ARG if count < 0. */
 int numarck_trace_events(void* const* events, int count);
 
+/* ---- self-test of the bounded device waits ----
+ * The only kernel that waits on other CTAs, the incompressible-offset scan (its decoupled
+ * look-back, §IV.C offsets), bounds every wait: after 2 s on the GPU's global timer it stores
+ * NUMARCK_ERR_TIMEOUT in the blob's status word and finishes, so a flag that is never set cannot
+ * hang the GPU. This entry point runs that same wait on a caller's flag: one single-thread
+ * kernel waits until the 8-byte word at flag_dev (device, 8-byte aligned) is non-zero, for at
+ * most limit_ns nanoseconds once its first 64 polls have failed, then stores NUMARCK_OK or
+ * NUMARCK_ERR_TIMEOUT into *status_dev (device int32). The kernel only reads the flag.
+ * limit_ns must lie in [1e6, 1e10] (1 ms to 10 s). Returns NUMARCK_ERR_INVALID_ARG for null or
+ * misaligned pointers or a limit out of range, NUMARCK_OK once the kernel is queued. */
+int numarck_selftest_wait(const void* flag_dev, int64_t limit_ns, int32_t* status_dev,
+                          numarck_stream_t stream);
+
 /* Human-readable name of a status code (static string). */
 const char* numarck_status_string(int code);
 

@@ -446,6 +446,18 @@ int numarck_decompress_compress(const void* blob, const void* header_host, const
   return launch_compress_tail(P, s);
 }
 
+int numarck_selftest_wait(const void* flag_dev, int64_t limit_ns, int32_t* status_dev,
+                          numarck_stream_t stream) {
+  if (!flag_dev || !status_dev || !aligned(flag_dev, 8) || !aligned(status_dev, 4))
+    return NUMARCK_ERR_INVALID_ARG;
+  if (limit_ns < 1000000 || limit_ns > 10000000000LL) return NUMARCK_ERR_INVALID_ARG;
+  if (launch_wait_selftest(static_cast<const unsigned long long*>(flag_dev),
+                           (unsigned long long)limit_ns, status_dev,
+                           reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return NUMARCK_ERR_CUDA;
+  return NUMARCK_OK;
+}
+
 int numarck_trace_events(void* const* events, int count) {
   if (count < 0) return NUMARCK_ERR_INVALID_ARG;
   g_trace = count ? events : nullptr;

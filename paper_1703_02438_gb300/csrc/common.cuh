@@ -176,6 +176,27 @@ __device__ __forceinline__ unsigned long long global_timer_ns() {
   return t;
 }
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+// Waits until ready(*p) holds (relaxed loads at GPU scope, backing off with nanosleep once 64
+// polls have failed), for at most limit_ns of the global timer from then on. Returns true with
+// the value in v, or false when the limit expires: every wait of a kernel on another CTA is
+// bounded this way, so a flag that is never set becomes an error status instead of a hang.
+template <typename Ready>
+__device__ __forceinline__ bool bounded_wait(const unsigned long long* p,
+                                             unsigned long long limit_ns, unsigned long long& v,
+                                             Ready ready) {
+  unsigned spins = 0;
+  unsigned long long t0 = 0;
+  for (;;) {
+    v = ld_relaxed_u64(p);
+    if (ready(v)) return true;
+    if (++spins == 64) t0 = global_timer_ns();
+    if (spins > 64) {
+      __nanosleep(100);
+      if ((spins & 63u) == 0 && global_timer_ns() - t0 > limit_ns) return false;
+    }
+  }
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

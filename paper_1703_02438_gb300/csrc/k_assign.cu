@@ -546,24 +546,15 @@ __global__ void __launch_bounds__(SC_THREADS, 1) k3_scan(const unsigned long lon
     } else {
       st_relaxed_u64(&flags[blk], SC_AGG | (unsigned long long)agg);
       long long j = blk - 1;
-      unsigned spins = 0;
-      unsigned long long t0 = 0;
       while (j >= 0) {
-        const unsigned long long sv = ld_relaxed_u64(&flags[j]);
-        const unsigned long long f = sv >> 62;
-        if (f == 0) {
-          if (++spins == 64) t0 = global_timer_ns();
-          if (spins > 64) {
-            __nanosleep(100);
-            if ((spins & 63u) == 0 && global_timer_ns() - t0 > SC_LIMIT_NS) {
-              atomicExch(blob_status, NUMARCK_ERR_TIMEOUT);
-              break;
-            }
-          }
-          continue;
+        unsigned long long sv = 0;
+        if (!bounded_wait(&flags[j], SC_LIMIT_NS, sv,
+                          [](unsigned long long x) { return (x >> 62) != 0ull; })) {
+          atomicExch(blob_status, NUMARCK_ERR_TIMEOUT);
+          break;
         }
         P += (long long)(sv & SC_VAL);
-        if (f == 2) break;
+        if ((sv >> 62) == 2) break;
         --j;
       }
       st_relaxed_u64(&flags[blk], SC_INC | (unsigned long long)(P + agg));
@@ -804,6 +795,22 @@ cudaError_t launch_exact(const CompressPlan& P, cudaStream_t s) {
 cudaError_t launch_assign(const CompressPlan& P, cudaStream_t s) {
   return P.g.dtype == NUMARCK_F64 ? launch_assign_t<double>(P, s, P.cd)
                                   : launch_assign_t<float>(P, s, P.cf);
+}
+
+namespace {
+// One thread runs the library's bounded wait on a caller's flag (numarck_selftest_wait).
+__global__ void k_wait_selftest(const unsigned long long* flag, unsigned long long limit_ns,
+                                int32_t* status) {
+  unsigned long long v = 0;
+  const bool ok = bounded_wait(flag, limit_ns, v, [](unsigned long long x) { return x != 0ull; });
+  *status = ok ? NUMARCK_OK : NUMARCK_ERR_TIMEOUT;
+}
+}  // namespace
+
+cudaError_t launch_wait_selftest(const unsigned long long* flag, unsigned long long limit_ns,
+                                 int32_t* status, cudaStream_t s) {
+  k_wait_selftest<<<1, 1, 0, s>>>(flag, limit_ns, status);
+  return cudaGetLastError();
 }
 
 }  // namespace nmk

@@ -66,6 +66,9 @@ cudaError_t launch_assign(const CompressPlan& P, cudaStream_t s);      // K3a: i
 cudaError_t launch_offsets(const CompressPlan& P, cudaStream_t s);     // K3b: offset tables
 cudaError_t launch_exact(const CompressPlan& P, cudaStream_t s);       // K3c: incompressible values
 cudaError_t launch_decode(const DecodePlan& P, cudaStream_t s);        // K4 / K5
+// one thread running the bounded device wait on a caller's flag (numarck_selftest_wait)
+cudaError_t launch_wait_selftest(const unsigned long long* flag, unsigned long long limit_ns,
+                                 int32_t* status, cudaStream_t s);
 // K41: decompression of D fused with K1 of the compression P of a new timestep against D's
 // output (zero-centred grid only)
 cudaError_t launch_step(const DecodePlan& D, const CompressPlan& P, cudaStream_t s);

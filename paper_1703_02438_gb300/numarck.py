@@ -122,6 +122,8 @@ def lib() -> ctypes.CDLL:
         L.numarck_decompress_compress.argtypes = [vp, vp, vp, vp, i64, vp, vp, pp, vp, sz, vp, sz,
                                                    vp]
         L.numarck_decompress_compress.restype = i32
+        L.numarck_selftest_wait.argtypes = [vp, i64, vp, vp]
+        L.numarck_selftest_wait.restype = i32
         L.numarck_status_string.argtypes = [i32]
         L.numarck_status_string.restype = ctypes.c_char_p
         L.numarck_trace_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), i32]
@@ -322,6 +324,16 @@ def decompress_compress(blob: torch.Tensor, prev: torch.Tensor, next_cur: torch.
         ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(_stream_ptr(stream))),
         "numarck_decompress_compress")
     return out, next_blob
+
+
+def selftest_wait(flag: torch.Tensor, limit_ns: int, status: torch.Tensor, stream=None) -> None:
+    """Queues the library's bounded device wait on `flag` (an int64 CUDA tensor): `status`
+    (int32 CUDA tensor) receives OK if the flag is non-zero within limit_ns, else ERR_TIMEOUT
+    (numarck_selftest_wait)."""
+    _check(lib().numarck_selftest_wait(ctypes.c_void_p(flag.data_ptr()), int(limit_ns),
+                                       ctypes.c_void_p(status.data_ptr()),
+                                       ctypes.c_void_p(_stream_ptr(stream))),
+           "numarck_selftest_wait")
 
 
 class Batch:

@@ -186,6 +186,17 @@ def test_chained_step_argument_errors_before_device(lib):
     assert C(hb=ctypes.c_char_p(bytes(bad))) == N.ERR_CORRUPT
 
 
+def test_selftest_wait_argument_errors(lib):
+    A = 1 << 20
+    W = lambda flag, limit, status: lib.numarck_selftest_wait(
+        ctypes.c_void_p(flag), limit, ctypes.c_void_p(status), None)
+    assert W(0, 10 ** 7, A) == N.ERR_INVALID_ARG                     # null flag
+    assert W(A, 10 ** 7, 0) == N.ERR_INVALID_ARG                     # null status
+    assert W(A + 4, 10 ** 7, A) == N.ERR_INVALID_ARG                 # flag not 8-byte aligned
+    assert W(A, 999_999, A) == N.ERR_INVALID_ARG                     # limit below 1 ms
+    assert W(A, 10 ** 10 + 1, A) == N.ERR_INVALID_ARG                # limit above 10 s
+
+
 def test_batch_validation_before_device(lib):
     """Batch calls validate every item on the host before queueing anything."""
     A = 1 << 20
