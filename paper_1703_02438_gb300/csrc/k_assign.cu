@@ -97,24 +97,21 @@ struct Bits<double> {
 
 constexpr int K3_WARPS = 32;                    // warps per CTA; each warp owns whole tiles
 constexpr int K3_THREADS = K3_WARPS * 32;
-constexpr int K3_SEG = 128;                     // elements per warp step: 4 consecutive per lane
-constexpr int K3_UNROLL = 4;                    // steps whose code loads are in flight together
+constexpr int K3_SEG = 128;                     // K3f's warp step: 4 consecutive points per lane
 constexpr int STEPS = SUB / 32;                 // 32-element ballot words per tile
 constexpr int K3_SMEM = 65536 * 2;              // index of every 16-bit code (bytes)
 
 // K3a — indexing and packing, from K1's codes alone. One warp processes one 4096-element tile at
-// a time (tile gw, gw + W, ... for global warp gw of W), in 128-element steps where lane l holds
-// elements 4l .. 4l+3: index = rank of the code's bin if the code says the point passed the
-// check of §III.C and the bin is selected, else the marker M (points with CODE_FAR are settled
-// from prev and cur). The lane's four B-bit indices form a 4B-bit field at bit 4Bl of the step's
-// image. When 4B is a multiple of 32 the lane stores its own words; otherwise output word w of
-// the image is assembled by lane w (and w - 32) from the fields that overlap it with warp
-// shuffles. Either way every store is coalesced (LSB-first order of §IV.C, zero padding to 16
-// bytes). The incompressible flags of each 32-element group go out as two 16-bit half-ballots
-// over the tile's own, already consumed codes (group s at u16 2s, 2s+1: 4s + 2 < 32 s + 32), and
-// the tile's count of incompressible points to the workspace. Tiles do not depend on each other
-// and there is no block-wide barrier after the rank table set-up. B is a template parameter so
-// that the packing is resolved at compile time.
+// a time (tile gw, gw + W, ... for global warp gw of W): index = rank of the code's bin if the
+// code says the point passed the check of §III.C and the bin is selected, else the marker M
+// (points with CODE_FAR are settled from prev and cur by K3f). Lane l of a step holds EL
+// consecutive points (k3a_tiles), so its indices fill whole words of the step's image and its
+// incompressible flags whole 16-bit half-ballot words (LSB-first order of §IV.C, zero padding to
+// 16 bytes). The flags of each 16-point group go over the tile's own, already consumed codes
+// (group h at u16 h of the tile's code area: h < 16 h + 16), and the tile's count of
+// incompressible points to the workspace. Tiles do not depend on each other and there is no
+// block-wide barrier after the rank table set-up. B is a template parameter so that the
+// packing is resolved at compile time.
 template <int B>
 struct Field {
   using type = typename std::conditional<(4 * B <= 32), unsigned, unsigned long long>::type;
@@ -217,19 +214,18 @@ __device__ __forceinline__ void anchor_consts(Consts<T>& c, const Geometry& g, c
 }
 
 
-// Codes e0 .. e0+15 of a tile (tile-relative) as eight words of two codes (the lower first), for
-// a lane whose 16 points all lie in the tile. The tile's codes start `sh` codes into the
-// 16-byte-aligned word `wb` of the codes array; a0, a1 are this lane's two aligned 16-byte words
-// (codes wb+e0 .. wb+e0+15) and b0 the next 16 bytes (the next lane's a0).
-__device__ __forceinline__ void shifted_codes(const uint4& a0, const uint4& a1, const uint4& b0,
-                                              int sh, unsigned (&cw)[8]) {
-  const unsigned win[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w,
-                            b0.x, b0.y, b0.z, b0.w};
+// Codes e0 .. e0+2NW-1 of a tile (tile-relative) as NW words of two codes (the lower first),
+// for a lane whose points all lie in the tile. The tile's codes start `sh` codes into the
+// 16-byte-aligned word `wb` of the codes array; win holds this lane's aligned words (codes
+// wb+e0 .. wb+e0+2NW-1) followed by the next 16 bytes (the next lane's first word).
+template <int NW>
+__device__ __forceinline__ void shifted_codes(const unsigned (&win)[NW + 4], int sh,
+                                              unsigned (&cw)[NW]) {
   const bool odd = sh & 1;
   switch (sh >> 1) {                             // uniform across the warp
 #define NMK_SHIFT_CASE(Q)                                                                     \
   case Q:                                                                                     \
-    _Pragma("unroll") for (int i = 0; i < 8; ++i)                                             \
+    _Pragma("unroll") for (int i = 0; i < NW; ++i)                                            \
       cw[i] = odd ? __funnelshift_r(win[i + Q], win[i + Q + 1], 16) : win[i + Q];              \
     break;
     NMK_SHIFT_CASE(0)
@@ -240,19 +236,20 @@ __device__ __forceinline__ void shifted_codes(const uint4& a0, const uint4& a1, 
   }
 }
 
-// K3a's tile loop for even B: 512-point steps in which lane l holds points 16l .. 16l+15, so that
-// its sixteen B-bit indices fill B/2 whole 32-bit words of the step's image (LSB first) and its
-// sixteen incompressible flags one 16-bit half-ballot word: the lane stores both itself, without
-// shuffles. Codes arrive as two 16-byte loads per lane (a tile that starts off a 16-byte boundary
-// funnel-shifts each lane's words with the next lane's). Lanes past the tile end, or whose codes
-// would reach past the codes array, read their codes one by one.
+// K3a's tile loop: steps of 32 EL points in which lane l holds points EL l .. EL l + EL - 1,
+// EL = 16 for even B and 32 for odd B, so that its EL B-bit indices fill EL B / 32 whole 32-bit
+// words of the step's image (LSB first) and its EL incompressible flags EL / 16 half-ballot
+// words: the lane stores both itself, without shuffles. Codes arrive as EL / 8 16-byte loads
+// per lane (a tile that starts off a 16-byte boundary funnel-shifts each lane's words with the
+// next lane's). Lanes past the tile end, or whose codes would reach past the codes array, read
+// their codes one by one.
 template <int B, typename T>
-__device__ __forceinline__ void k3a_tiles_even(const AssignArgs<T>& A,
-                                               const unsigned short* s_tab, long long W, int lane,
-                                               int tid, int any) {
+__device__ __forceinline__ void k3a_tiles(const AssignArgs<T>& A, const unsigned short* s_tab,
+                                          long long W, int lane, int tid, int any) {
   constexpr unsigned M = (1u << B) - 1u;
   constexpr bool kSentinel = B < 16;             // see k3_assign
-  constexpr int EL = 16, WL = B / 2, SEGW = 32 * EL;
+  constexpr int EL = B % 2 == 0 ? 16 : 32, NW = EL / 2, NV = EL / 8, WL = EL * B / 32;
+  constexpr int SEGW = 32 * EL;
   const Geometry& g = A.g;
   for (long long gt = (long long)blockIdx.x * K3_WARPS + (tid >> 5); gt < g.nsub; gt += W) {
     const TileRef tr = tile_ref<B>(g, gt, A.blob, A.codes);
@@ -265,28 +262,33 @@ __device__ __forceinline__ void k3a_tiles_even(const AssignArgs<T>& A,
     unsigned far = 0;
     for (int sb0 = 0; sb0 < cnt; sb0 += SEGW) {
       const int e0 = sb0 + EL * lane;
-      unsigned cw[8];
       const long long w0 = wb + e0;              // this lane's first aligned code
-      uint4 a0 = make_uint4(0u, 0u, 0u, 0u), a1 = a0;
-      if (w0 + 8 <= g.n) a0 = __ldcs(cw4 + (e0 >> 3));
-      if (w0 + 16 <= g.n) a1 = __ldcs(cw4 + (e0 >> 3) + 1);
-      uint4 b0;
-      b0.x = __shfl_down_sync(0xffffffffu, a0.x, 1);
-      b0.y = __shfl_down_sync(0xffffffffu, a0.y, 1);
-      b0.z = __shfl_down_sync(0xffffffffu, a0.z, 1);
-      b0.w = __shfl_down_sync(0xffffffffu, a0.w, 1);
+      unsigned win[NW + 4];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        uint4 a = make_uint4(0u, 0u, 0u, 0u);
+        if (w0 + 8 * (v + 1) <= g.n) a = __ldcs(cw4 + (e0 >> 3) + v);
+        win[4 * v] = a.x; win[4 * v + 1] = a.y; win[4 * v + 2] = a.z; win[4 * v + 3] = a.w;
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) win[NW + i] = __shfl_down_sync(0xffffffffu, win[i], 1);
       const bool inside = e0 + EL <= cnt;
-      if (lane == 31 && sh && inside && w0 + 24 <= g.n) b0 = __ldcs(cw4 + (e0 >> 3) + 2);
-      if (inside && (sh == 0 || w0 + 24 <= g.n)) {
+      const bool whole = w0 + EL + (sh ? 8 : 0) <= g.n;
+      if (lane == 31 && sh && inside && whole) {
+        const uint4 b = __ldcs(cw4 + (e0 >> 3) + NV);
+        win[NW] = b.x; win[NW + 1] = b.y; win[NW + 2] = b.z; win[NW + 3] = b.w;
+      }
+      unsigned cw[NW];
+      if (inside && whole) {
         if (sh == 0) {
-          cw[0] = a0.x; cw[1] = a0.y; cw[2] = a0.z; cw[3] = a0.w;
-          cw[4] = a1.x; cw[5] = a1.y; cw[6] = a1.z; cw[7] = a1.w;
+#pragma unroll
+          for (int i = 0; i < NW; ++i) cw[i] = win[i];
         } else {
-          shifted_codes(a0, a1, b0, sh, cw);
+          shifted_codes<NW>(win, sh, cw);
         }
       } else {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < NW; ++i) {
           const unsigned lo = e0 + 2 * i < cnt ? (unsigned)ct[e0 + 2 * i] : CODE_NONE;
           const unsigned hi = e0 + 2 * i + 1 < cnt ? (unsigned)ct[e0 + 2 * i + 1] : CODE_NONE;
           cw[i] = lo | (hi << 16);
@@ -316,7 +318,9 @@ __device__ __forceinline__ void k3a_tiles_even(const AssignArgs<T>& A,
         w[bit >> 5] |= idx << (bit & 31);
         if ((bit & 31) + B > 32) w[(bit >> 5) + 1] |= idx >> (32 - (bit & 31));
       }
-      if (e0 < cnt) tr.halves[e0 >> 4] = (unsigned short)fl;
+#pragma unroll
+      for (int h = 0; h < EL / 16; ++h)
+        if (e0 + 16 * h < cnt) tr.halves[(e0 >> 4) + h] = (unsigned short)(fl >> (16 * h));
       count += __popc(fl);
       const int ow = (sb0 / SEGW) * (32 * WL) + lane * WL;   // first word of the lane's fields
       if (ow < tr.twords) {
@@ -350,7 +354,6 @@ __global__ void __launch_bounds__(K3_THREADS, 1) k3_assign(AssignArgs<T> A) {
   constexpr unsigned FARV = kSentinel ? 0xFFFFu : M;
   extern __shared__ __align__(16) unsigned short s_tab[];   // [65536]: index of each code
 
-  const Geometry& g = A.g;
   const Ctrl* ctrl = A.ctrl;
   const int tid = (int)threadIdx.x;
   const int lane = (int)lane_id();
@@ -369,85 +372,7 @@ __global__ void __launch_bounds__(K3_THREADS, 1) k3_assign(AssignArgs<T> A) {
   __syncthreads();   // the only block-wide barriers: the table is read-only from here on
 
   const long long W = (long long)gridDim.x * K3_WARPS;
-  if constexpr (B % 2 == 0) {
-    k3a_tiles_even<B>(A, s_tab, W, lane, tid, any);
-  } else {
-  for (long long gt = (long long)blockIdx.x * K3_WARPS + (tid >> 5); gt < g.nsub; gt += W) {
-    const TileRef tr = tile_ref<B>(g, gt, A.blob, A.codes);
-    const int cnt = tr.cnt;
-    const unsigned short* ct = A.codes + tr.j0;
-    // codes are read as 8-byte words aligned in the codes array: a tile that starts sh codes
-    // past such a word takes each lane's four codes from its word and the next lane's
-    const int sh = (int)(tr.j0 & 3);
-    const long long wbase = tr.j0 - sh;          // first aligned word of the tile (in codes)
-    const unsigned short* cw = A.codes + wbase;
-    int count = 0;
-    unsigned far = 0;                            // > M (B < 16) or non-zero: CODE_FAR seen
-    for (int s0 = 0; s0 < cnt; s0 += K3_SEG * K3_UNROLL) {
-      uint2 cd[K3_UNROLL];   // four 16-bit codes per lane and step
-      if (sh == 0) {                             // uniform across the warp
-#pragma unroll
-        for (int u = 0; u < K3_UNROLL; ++u) {
-          const int e0 = s0 + u * K3_SEG + lane * 4;
-          if (e0 + 4 <= cnt) {
-            cd[u] = __ldcs(reinterpret_cast<const uint2*>(ct + e0));
-          } else {
-            unsigned v[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) v[k] = e0 + k < cnt ? (unsigned)ct[e0 + k] : CODE_NONE;
-            cd[u] = make_uint2(v[0] | (v[1] << 16), v[2] | (v[3] << 16));
-          }
-        }
-      } else {
-#pragma unroll
-        for (int u = 0; u < K3_UNROLL; ++u) {
-          const int e0 = s0 + u * K3_SEG + lane * 4;
-          const long long w0 = wbase + e0;       // this lane's aligned word (in codes)
-          const uint2 lo = w0 + 4 <= g.n ? __ldcs(reinterpret_cast<const uint2*>(cw + e0))
-                                         : make_uint2(0u, 0u);
-          uint2 hi;
-          hi.x = __shfl_down_sync(0xffffffffu, lo.x, 1);
-          hi.y = __shfl_down_sync(0xffffffffu, lo.y, 1);
-          const bool vec = e0 + 4 <= cnt && w0 + 8 <= g.n;   // both words in the codes array
-          if (lane == 31 && vec) hi = __ldcs(reinterpret_cast<const uint2*>(cw + e0 + 4));
-          if (vec) {
-            const unsigned long long L = ((unsigned long long)lo.y << 32) | lo.x;
-            const unsigned long long H = ((unsigned long long)hi.y << 32) | hi.x;
-            const unsigned long long V = (L >> (16 * sh)) | (H << (64 - 16 * sh));
-            cd[u] = make_uint2((unsigned)V, (unsigned)(V >> 32));
-          } else {
-            unsigned v[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) v[k] = e0 + k < cnt ? (unsigned)ct[e0 + k] : CODE_NONE;
-            cd[u] = make_uint2(v[0] | (v[1] << 16), v[2] | (v[3] << 16));
-          }
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < K3_UNROLL; ++u) {
-        const int sb0 = s0 + u * K3_SEG;
-        if (sb0 >= cnt) break;                   // uniform across the warp
-        unsigned idx[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const unsigned cv = ((k < 2 ? cd[u].x : cd[u].y) >> (16 * (k & 1))) & 0xFFFFu;
-          const unsigned r = s_tab[cv];
-          if constexpr (kSentinel) {
-            far = max(far, r);
-            idx[k] = min(r, M);
-          } else {
-            far |= cv == CODE_FAR ? 1u : 0u;
-            idx[k] = r;
-          }
-        }
-        step_out<B>(idx, sb0, cnt, lane, tr.halves, tr.tw, tr.twords, count);
-      }
-    }
-    count = __reduce_add_sync(0xffffffffu, count);
-    const bool fix = any && __any_sync(0xffffffffu, kSentinel ? far > M : far != 0u);
-    if (lane == 0) A.tstatus[gt] = (unsigned long long)count | (fix ? K3_FAR_FLAG : 0ull);
-  }
-  }
+  k3a_tiles<B>(A, s_tab, W, lane, tid, any);
 }
 
 // K3f — tiles with points outside K1's code window (flagged by K3a; rare: a bin more than 16383
