@@ -57,7 +57,7 @@ __device__ __forceinline__ void st4(float* p, const float* v) {
   __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
 }
 
-constexpr int K4_WARPS = 16;                    // warps per CTA (each owns whole tiles)
+constexpr int K4_WARPS = 16;                    // warps per CTA (each owns a sub-block or a part)
 constexpr int K4_THREADS = K4_WARPS * 32;
 constexpr int K4_SEG = 128;                     // elements per warp step: 4 consecutive per lane
 // steps whose loads are in flight together: float32 moves half the bytes per load, so it

@@ -1,7 +1,8 @@
 // k_decode.cu — K4/K5: decompression (§III.E, Eq. 4 read as R = prev * (1 + centre)) and
 // partial decompression of a segment (§IV.C, §V.C).
 //
-// One warp decodes one 4096-element tile (sub-block) at a time, in 128-element steps where lane
+// One warp decodes one 4096-element tile (sub-block), or one of 2, 4 or 8 parts of it when a
+// variable has too few tiles to fill the GPU (see seg_log2_for), in 128-element steps where lane
 // l owns elements 4l .. 4l+3: it reads its 4B-bit field of the step's packed image (one word
 // when B = 8, two when B = 16, else the two or three words the field overlaps), splits it into
 // four indices, numbers the incompressible points of the step in element order with four

@@ -23,7 +23,7 @@ namespace nmk {
 
 namespace {
 
-constexpr int K41_WARPS = 16;                    // warps per CTA (each owns whole tiles)
+constexpr int K41_WARPS = 16;                    // warps per CTA (each owns a sub-block or a part)
 constexpr int K41_THREADS = K41_WARPS * 32;
 
 struct StepArgs {
