@@ -24,9 +24,6 @@ constexpr int HWIN = (1 << (WIN_LOG2 + 1)) + 16; // global histogram window (bin
 constexpr int HMARGIN = 8;                      // spare bins at each end of the window
 constexpr int SH_BINS = 16384;                  // K1 shared-memory histogram window
 constexpr int DM_SMEM = 4096;                   // K4 multipliers kept in shared memory
-constexpr int TILE_THREADS = 512;               // K3/K4 block size
-constexpr int EPT = SUB / TILE_THREADS;         // elements per thread per tile (8)
-constexpr int NCHUNK = EPT * (TILE_THREADS / 32); // 32-element chunks per tile (128)
 constexpr unsigned KEY_BIAS = 0x40000000u;      // bin-range keys: 0 means "no value"
 // Per-element codes written by K1 and read by K3. For a binnable point whose bin b lies in the
 // code window [code_base, code_base + CODE_BINS) (code_base = zero-change bin - 16383):
@@ -328,36 +325,6 @@ __device__ __forceinline__ bool ratio_estimate(unsigned ph, unsigned pl, int ep,
   return e32 < 255;
 }
 
-// Fast part of classify_f64: 1 and the bin, 0 (not binnable), or 2 when only the exact float64
-// sequence can decide (classify_exact then gives the answer). Never calls the exact sequence.
-__device__ __forceinline__ int classify_f64_fast(double p, double x, const Consts<double>& c,
-                                                 int& b) {
-  const unsigned ph = (unsigned)__double2hiint(p), pl = (unsigned)__double2loint(p);
-  const unsigned xh = (unsigned)__double2hiint(x);
-  const int ep = (int)((ph >> 20) & 0x7FFu);
-  const int ex = (int)((xh >> 20) & 0x7FFu);
-  if ((unsigned)(ep - 200) <= 1740u && ex != 0x7FF) {
-    float Df;
-    if (!ratio_estimate(ph, pl, ep, p, x, Df)) return 0;   // |d/s| >= 2^128: far beyond the cap
-    const float aD = fabsf(Df);
-    if (aD > c.cap_hi) return 0;                           // certainly |ratio| > cap
-    if (aD <= c.cap_lo) {                                  // certainly binnable
-      const float uf = __fmul_rn(__fsub_rn(Df, c.af), c.inv_wf);
-      const float eps = __fmaf_ru(0x1.8p-20f, fabsf(uf), c.K0);
-      const float lo = floorf(__fsub_rd(uf, eps));
-      const float hi = floorf(__fadd_ru(uf, eps));
-      if (lo == hi && lo < 4194304.0f) {
-        b = __float_as_int(__fadd_rn(lo, 12582912.0f)) - 0x4B400000;   // exact for |lo| < 2^22
-        return 1;
-      }
-    }
-    return 2;
-  }
-  if ((ph << 1) == 0u && pl == 0u) return 0;               // p = +-0: ratio is +-inf or NaN
-  if (ep == 0x7FF || ex == 0x7FF) return 0;                // non-finite input
-  return 2;
-}
-
 // Bin of (p, x) for float64: 1 and the bin if binnable, else 0. Equal to classify_exact<double>.
 __device__ __forceinline__ int classify_f64(double p, double x, const Consts<double>& c, int& b) {
   const unsigned ph = (unsigned)__double2hiint(p), pl = (unsigned)__double2loint(p);
@@ -399,29 +366,32 @@ __device__ __forceinline__ int classify_f64(double p, double x, const Consts<dou
 // deltaH = 2^-21 H + 2^-20 Ef |Df| + 2^-100 covers the second. If |G| + delta < H - deltaH the
 // exact check passes; if |G| - delta > H + deltaH it fails; otherwise the exact float64 check
 // decides. (All bound arithmetic rounds away from the decision.)
-// 1 = the check passes, 0 = it fails, 2 = the estimate cannot decide (then run check_exact).
-__device__ __forceinline__ int check_f64_fast(double p, double x, float cf,
-                                              const Consts<double>& c) {
+// The check with that rule, falling back to the exact float64 sequence when it cannot decide.
+__device__ __forceinline__ bool check_f64(double p, double x, double m, float cf,
+                                          const Consts<double>& c) {
   const unsigned ph = (unsigned)__double2hiint(p), pl = (unsigned)__double2loint(p);
   const unsigned xh = (unsigned)__double2hiint(x);
   const int ep = (int)((ph >> 20) & 0x7FFu);
   const int ex = (int)((xh >> 20) & 0x7FFu);
-  float Df;
-  const bool est = ratio_estimate(ph, pl, ep, p, x, Df);
-  const float aDf = fabsf(Df);
-  const float G = __fsub_rn(cf, Df);
-  const float aG = fabsf(G);
-  const float H = __fmul_rn(c.Ef, fabsf(__fadd_rn(1.0f, Df)));
-  const float delta = __fmaf_ru(0x1p-23f, __fadd_ru(fabsf(cf), aG),
-                                __fmaf_ru(0x1p-20f, aDf, __fmaf_ru(0x1p-50f, fabsf(cf), 0x1p-49f)));
-  const float dH = __fmaf_ru(0x1p-21f, H, __fmaf_ru(0x1p-20f * c.Ef, aDf, 0x1p-100f));
-  const bool in_range = (unsigned)(ep - 200) <= 1740u && (unsigned)(ex - 100) <= 1840u && est;
-  const bool yes = __fadd_ru(aG, delta) < __fsub_rd(H, dH);
-  const bool no = __fsub_rd(aG, delta) > __fadd_ru(H, dH);
-  return !in_range ? 2 : (yes ? 1 : (no ? 0 : 2));
+  if ((unsigned)(ep - 200) <= 1740u && (unsigned)(ex - 100) <= 1840u) {
+    float Df;
+    if (ratio_estimate(ph, pl, ep, p, x, Df)) {
+      const float aDf = fabsf(Df);
+      const float G = __fsub_rn(cf, Df);
+      const float aG = fabsf(G);
+      const float H = __fmul_rn(c.Ef, fabsf(__fadd_rn(1.0f, Df)));
+      const float delta = __fmaf_ru(0x1p-23f, __fadd_ru(fabsf(cf), aG),
+                                    __fmaf_ru(0x1p-20f, aDf,
+                                              __fmaf_ru(0x1p-50f, fabsf(cf), 0x1p-49f)));
+      const float dH = __fmaf_ru(0x1p-21f, H, __fmaf_ru(0x1p-20f * c.Ef, aDf, 0x1p-100f));
+      if (__fadd_ru(aG, delta) < __fsub_rd(H, dH)) return true;
+      if (__fsub_rd(aG, delta) > __fadd_ru(H, dH)) return false;
+    }
+  }
+  return check_exact_f64_slow(p, x, m, c.E_T);
 }
 
-// K1's fused float64 step: the bin of (p, x) as classify_f64_fast decides it and, for a bin in
+// K1's fused float64 step: the bin of (p, x) as classify_f64's estimate decides it and, for a bin in
 // the code window, the check of §III.C against that bin's own centre, decided from the same
 // ratio estimate Df. The multiplier is estimated in float32 from the bin id:
 //   v = b + 1/2 (exact), Q = fl32(v * wf), cfe = fl32(af + Q),
@@ -430,7 +400,7 @@ __device__ __forceinline__ int check_f64_fast(double p, double x, float cf,
 //   |cfe - (a + v w)| <= 1.07 * 2^-24 |cfe| + 2^-24 |a| + 2.0001 * 2^-24 |v w|,
 // and as |a| <= |af| (1 + 2^-23), |v w| <= |Q| (1 + 2^-22):
 //   |cfe - c'| <= Kc = 2^-22 (|cfe| + |af| + 2 |Q|) + 2^-50               (rounded upward),
-// which takes the place of the rounding of cf in check_f64_fast's bound: the same decision rule
+// which takes the place of the rounding of cf in check_f64's bound: the same decision rule
 // with G = fl(cfe - Df) and delta + Kc is exact. The terms of delta + Kc and dH are regrouped
 // below into one per-bin term and one term in |Df| (each rounded upward, so every comparison
 // implies the one it replaces).
@@ -474,30 +444,6 @@ __device__ __forceinline__ int classify_check_f64_fast(double p, double x, const
   const bool never = ((ph << 1) == 0u && pl == 0u) || ep == 0x7FF || ex == 0x7FF;
   return in_range ? (beyond ? 0 : (!sure ? 2 : ((outside || decided) ? 1 : 3)))
                   : (never ? 0 : 2);
-}
-
-__device__ __forceinline__ bool check_f64(double p, double x, double m, float cf,
-                                          const Consts<double>& c) {
-  const unsigned ph = (unsigned)__double2hiint(p), pl = (unsigned)__double2loint(p);
-  const unsigned xh = (unsigned)__double2hiint(x);
-  const int ep = (int)((ph >> 20) & 0x7FFu);
-  const int ex = (int)((xh >> 20) & 0x7FFu);
-  if ((unsigned)(ep - 200) <= 1740u && (unsigned)(ex - 100) <= 1840u) {
-    float Df;
-    if (ratio_estimate(ph, pl, ep, p, x, Df)) {
-      const float aDf = fabsf(Df);
-      const float G = __fsub_rn(cf, Df);
-      const float aG = fabsf(G);
-      const float H = __fmul_rn(c.Ef, fabsf(__fadd_rn(1.0f, Df)));
-      const float delta = __fmaf_ru(0x1p-23f, __fadd_ru(fabsf(cf), aG),
-                                    __fmaf_ru(0x1p-20f, aDf,
-                                              __fmaf_ru(0x1p-50f, fabsf(cf), 0x1p-49f)));
-      const float dH = __fmaf_ru(0x1p-21f, H, __fmaf_ru(0x1p-20f * c.Ef, aDf, 0x1p-100f));
-      if (__fadd_ru(aG, delta) < __fsub_rd(H, dH)) return true;
-      if (__fsub_rd(aG, delta) > __fadd_ru(H, dH)) return false;
-    }
-  }
-  return check_exact_f64_slow(p, x, m, c.E_T);
 }
 
 // ------------------------------------------------------------------------------------------
