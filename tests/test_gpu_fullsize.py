@@ -159,3 +159,29 @@ def test_fullsize_flash_pair(series, E, B):
     torch.cuda.synchronize()
     assert torch.equal(seg.view(torch.int64), rec[s: s + c].view(torch.int64))
     assert int(status.item()) == 0
+
+
+@pytest.mark.parametrize("E,B", [(1e-4, 10), (1e-3, 8)])
+def test_fullsize_chained_step_equals_separate_calls(series, E, B):
+    """At the full size and in the launch configuration of the timed run, the chained step
+    (decompression fused with the next compression's first pass) gives byte for byte the
+    reconstruction and the next blob of the separate calls, whose parity with the oracle the
+    test above establishes. The next timestep is the pair's cur scaled by a smooth factor, so
+    its ratios against the reconstruction spread over many bins."""
+    p_dev, x_dev = series
+    n = p_dev.numel()
+    idx = torch.arange(n, device=DEV, dtype=torch.float64)
+    y_dev = x_dev * (1.0 + 3e-3 * torch.sin(idx * 1e-5))
+    del idx
+    b1 = N.compress(p_dev, x_dev, E, B)
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    rec_sep = N.decompress(b1, p_dev, status=status)
+    sep = N.compress(rec_sep, y_dev, E, B)
+    torch.cuda.synchronize()
+    sep_bytes = sep[:N.blob_size(N.header_bytes(sep))]
+    rec, nxt = N.decompress_compress(b1, p_dev, y_dev, E, B, status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert torch.equal(rec.view(torch.int64), rec_sep.view(torch.int64))
+    got = nxt[:N.blob_size(N.header_bytes(nxt))]
+    assert got.numel() == sep_bytes.numel() and torch.equal(got, sep_bytes)
