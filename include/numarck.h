@@ -418,7 +418,7 @@ typedef struct numarck_zindex_header {
 
 /* Bytes a container can need for the blob whose header (host copy) is given; 0 if invalid. */
 size_t numarck_zindex_bound(const void* blob_header_host);
-/* Device workspace bytes numarck_deflate_index needs (16 per sub-block); 0 if invalid. */
+/* Device workspace bytes numarck_deflate_index needs (80 per sub-block); 0 if invalid. */
 size_t numarck_zindex_workspace_bytes(const void* blob_header_host);
 /* Deflates the index section of a compressed blob (device, with its header's host copy) into
  * zindex (device, zcap >= numarck_zindex_bound, 256-byte aligned). Asynchronous on stream;

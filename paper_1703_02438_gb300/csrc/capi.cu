@@ -485,7 +485,7 @@ size_t numarck_zindex_bound(const void* header_host) {
 size_t numarck_zindex_workspace_bytes(const void* header_host) {
   Geometry g;
   if (blob_geometry(header_host, &g)) return 0;
-  return (size_t)std::max<int64_t>(256, g.nsub * 16);
+  return (size_t)std::max<int64_t>(256, g.nsub * (16 + 64));   // see launch_deflate
 }
 
 int numarck_deflate_index(const void* blob, const void* header_host, void* zindex, size_t zcap,

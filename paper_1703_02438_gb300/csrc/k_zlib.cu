@@ -30,10 +30,12 @@ namespace nmk {
 
 namespace {
 
-constexpr int ZW = 2;                             // warps per CTA (one sub-block each)
+constexpr int ZW = 4;                             // warps per CTA (one sub-block each)
 constexpr int ZT = ZW * 32;
-constexpr int Z_IN = SUB / 8 * NUMARCK_MAX_B;     // largest sub-block image (bytes)
-constexpr int Z_OUT_WORDS = (Z_IN * 9 + 64 + 31) / 32 + 4;   // all literals of 9 bits + tail
+// per warp: the sub-block's image (SUB/8 * B bytes) and, in Z3, its codes (every byte a 9-bit
+// literal at worst, plus the block header and tail); shared memory is sized for the blob's B
+__host__ __device__ constexpr int z_in_bytes(int B) { return SUB / 8 * B; }
+__host__ __device__ constexpr int z_out_words(int B) { return (z_in_bytes(B) * 9 + 64 + 31) / 32 + 4; }
 constexpr unsigned ADLER = 65521u;
 static_assert(sizeof(numarck_zindex_header) == NUMARCK_ZINDEX_HEADER_BYTES, "container header");
 
@@ -96,6 +98,34 @@ struct BitWriter {
   }
 };
 
+// One lane's codes, written from a register accumulator: the words that only this lane writes
+// are stored whole; its first word (shared with the codes before it) and its last (shared with
+// the codes after it) are or-ed in. The words must be zero beforehand.
+struct LaneBits {
+  unsigned* w;
+  int wi;                 // word the accumulator's bit 0 belongs to
+  int first;              // this lane's first word
+  unsigned long long acc;
+  int nacc;               // bits held in acc (including the lane's offset into its first word)
+  __device__ __forceinline__ LaneBits(unsigned* w_, int bitpos)
+      : w(w_), wi(bitpos >> 5), first(bitpos >> 5), acc(0ull), nacc(bitpos & 31) {}
+  __device__ __forceinline__ void put(unsigned v, int n) {   // n <= 25 bits, LSB first
+    if (n == 0) return;
+    acc |= (unsigned long long)v << nacc;
+    nacc += n;
+    if (nacc >= 32) {
+      if (wi == first) atomicOr(&w[wi], (unsigned)acc);
+      else w[wi] = (unsigned)acc;
+      ++wi;
+      acc >>= 32;
+      nacc -= 32;
+    }
+  }
+  __device__ __forceinline__ void flush() {
+    if (nacc > 0) atomicOr(&w[wi], (unsigned)acc);
+  }
+};
+
 struct ZArgs {
   const unsigned char* blob;
   Geometry g;
@@ -103,6 +133,7 @@ struct ZArgs {
   int64_t* tile_bytes;       // per sub-block: its slot's bytes (Z1), then its offset (Z2)
   unsigned* adler_a;         // per sub-block: sum of bytes mod 65521
   unsigned* adler_w;         // per sub-block: sum of (size - j) * byte_j mod 65521
+  unsigned short* lane_bits; // per sub-block and lane: bits of the lane's codes (Z1 for Z3)
   numarck_zindex_header zh;  // container header (written into the container by Z2)
 };
 
@@ -132,7 +163,8 @@ __device__ __forceinline__ ZTile ztile(const ZArgs& A, long long gt) {
 
 // Greedy parse of bytes [c0, c1) of s with matches at distance p; bits of the codes, and (when
 // bw is given) the codes themselves.
-__device__ int parse_chunk(const unsigned char* s, int c0, int c1, int p, BitWriter* bw) {
+template <typename Writer>
+__device__ int parse_chunk(const unsigned char* s, int c0, int c1, int p, Writer* bw) {
   int bits = 0;
   int i = c0;
   while (i < c1) {
@@ -182,10 +214,10 @@ __device__ __forceinline__ long long slot_bytes(int data_bytes, bool first, bool
 
 // Z1: per sub-block, the slot size and the Adler-32 partial sums.
 __global__ void __launch_bounds__(ZT) z1_size(ZArgs A) {
-  __shared__ __align__(16) unsigned char s_in[ZW][Z_IN];
+  extern __shared__ __align__(16) unsigned char z_smem[];
   const int lane = (int)lane_id(), warp = (int)(threadIdx.x >> 5);
   const int p = period_of(A.g.B);
-  unsigned char* s = s_in[warp];
+  unsigned char* s = z_smem + warp * z_in_bytes(A.g.B);
   for (long long gt = (long long)blockIdx.x * ZW + warp; gt < A.g.nsub;
        gt += (long long)gridDim.x * ZW) {
     const ZTile z = ztile(A, gt);
@@ -194,7 +226,8 @@ __global__ void __launch_bounds__(ZT) z1_size(ZArgs A) {
     __syncwarp();
     const int per = (z.tb + 31) / 32;
     const int c0 = min(z.tb, lane * per), c1 = min(z.tb, c0 + per);
-    int bits = parse_chunk(s, c0, c1, p, nullptr);
+    int bits = parse_chunk<LaneBits>(s, c0, c1, p, nullptr);
+    A.lane_bits[gt * 32 + lane] = (unsigned short)bits;
     unsigned a = 0;
     unsigned long long w = 0;
     for (int i = lane; i < z.tb; i += 32) {
@@ -271,22 +304,20 @@ __global__ void __launch_bounds__(1024) z2_scan(ZArgs A) {
 
 // Z3: writes every slot (zlib header, the sub-block's DEFLATE data, stream trailer).
 __global__ void __launch_bounds__(ZT) z3_write(ZArgs A) {
-  __shared__ __align__(16) unsigned char s_in[ZW][Z_IN];
-  __shared__ __align__(16) unsigned s_out[ZW][Z_OUT_WORDS];
+  extern __shared__ __align__(16) unsigned char z_smem[];
   const int lane = (int)lane_id(), warp = (int)(threadIdx.x >> 5);
   const int p = period_of(A.g.B);
-  unsigned char* s = s_in[warp];
-  unsigned* o = s_out[warp];
+  const int inb = z_in_bytes(A.g.B), outw = z_out_words(A.g.B);
+  unsigned char* s = z_smem + warp * inb;
+  unsigned* o = reinterpret_cast<unsigned*>(z_smem + ZW * inb) + warp * outw;
   for (long long gt = (long long)blockIdx.x * ZW + warp; gt < A.g.nsub;
        gt += (long long)gridDim.x * ZW) {
     const ZTile z = ztile(A, gt);
     for (int i = lane; i < z.padded / 16; i += 32)
       reinterpret_cast<uint4*>(s)[i] = __ldg(reinterpret_cast<const uint4*>(z.src) + i);
-    for (int i = lane; i < Z_OUT_WORDS; i += 32) o[i] = 0u;
-    __syncwarp();
     const int per = (z.tb + 31) / 32;
     const int c0 = min(z.tb, lane * per), c1 = min(z.tb, c0 + per);
-    const int bits = parse_chunk(s, c0, c1, p, nullptr);
+    const int bits = A.lane_bits[gt * 32 + lane];    // Z1's count of this lane's code bits
     int incl = bits;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -294,6 +325,10 @@ __global__ void __launch_bounds__(ZT) z3_write(ZArgs A) {
       if (lane >= d) incl += u;
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
+    // the words the codes (header, codes, end of block, stored-block header bits) touch start at 0
+    const int used_words = (3 + total + 10 + 31) / 32 + 1;
+    for (int i = lane; i < used_words; i += 32) o[i] = 0u;
+    __syncwarp();
     const long long off = A.tile_bytes[gt];
     unsigned char* dst = A.z + off;
     const int k = z.first ? 2 : 0;
@@ -309,12 +344,13 @@ __global__ void __launch_bounds__(ZT) z3_write(ZArgs A) {
       for (int i = lane; i < z.tb; i += 32) dst[k + 5 + i] = s[i];
       nb = stored_bytes(z.tb);
     } else {
-      BitWriter bw{o, 3 + incl - bits};
+      LaneBits bw(o, 3 + incl - bits);
       if (lane == 0) {
         BitWriter hw{o, 0};
         hw.put(2u, 3);                       // BFINAL 0, BTYPE 01 (fixed Huffman)
       }
       parse_chunk(s, c0, c1, p, &bw);
+      bw.flush();
       __syncwarp();
       int end_bits = 3 + total;
       if (lane == 0) {
@@ -333,23 +369,30 @@ __global__ void __launch_bounds__(ZT) z3_write(ZArgs A) {
       }
       nb = cb + 4;
     }
-    if (lane == 0) {
-      unsigned char* tail = dst + k + nb;
-      if (z.last) {
+    if (z.last) {
+      // Adler-32 of the block from its sub-blocks' partial sums (the lanes share them out): with
+      // N the block's bytes and `after` the bytes of the block after sub-block u,
+      // a = 1 + sum_u a_u, b = N + sum_u (after_u * a_u + w_u) (mod 65521). Every sub-block
+      // before the last one of a block is full (SUB/8 * B bytes).
+      const long long g0 = z.q * A.g.spb;
+      const long long full = SUB / 8 * A.g.B;
+      unsigned long long sa = 0, sb = 0;
+      for (long long u = g0 + lane; u <= gt; u += 32) {
+        const long long after = u == gt ? 0 : (long long)z.tb + (gt - 1 - u) * full;
+        sa += A.adler_a[u];
+        sb += ((unsigned long long)(after % ADLER) * A.adler_a[u] + A.adler_w[u]) % ADLER;
+      }
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) {
+        sa += __shfl_xor_sync(0xffffffffu, sa, d);
+        sb += __shfl_xor_sync(0xffffffffu, sb, d);
+      }
+      if (lane == 0) {
+        unsigned char* tail = dst + k + nb;
         tail[0] = 0x03; tail[1] = 0x00;    // empty fixed-Huffman block with BFINAL 1
-        // Adler-32 of the block: combine its sub-blocks' partial sums in order
-        const long long g0 = z.q * A.g.spb;
-        unsigned long long sa = 1, sb = 0;
-        long long after = 0;               // bytes of the block after the current sub-block
-        for (long long u = gt; u >= g0; --u) {
-          const ZTile zu = ztile(A, u);
-          sa += A.adler_a[u];
-          sb += ((unsigned long long)(after % ADLER) * A.adler_a[u] + A.adler_w[u]) % ADLER;
-          after += zu.tb;
-        }
-        // b = sum over bytes of (N - j) * byte_j + N, with N the block size
-        sb = (sb + (unsigned long long)(after % ADLER)) % ADLER;
-        sa %= ADLER;
+        const long long N = (long long)z.tb + (gt - g0) * full;
+        sb = (sb + (unsigned long long)(N % ADLER)) % ADLER;
+        sa = (1 + sa) % ADLER;
         const unsigned ad = (unsigned)((sb << 16) | sa);
         tail[2] = (unsigned char)(ad >> 24); tail[3] = (unsigned char)(ad >> 16);
         tail[4] = (unsigned char)(ad >> 8);  tail[5] = (unsigned char)ad;
@@ -564,11 +607,26 @@ cudaError_t launch_deflate(const unsigned char* blob, const Geometry& g, unsigne
   A.tile_bytes = reinterpret_cast<int64_t*>(ws);
   A.adler_a = reinterpret_cast<unsigned*>(ws + g.nsub * 8);
   A.adler_w = A.adler_a + g.nsub;
+  A.lane_bits = reinterpret_cast<unsigned short*>(ws + g.nsub * 16);
+  const size_t smem1 = (size_t)ZW * z_in_bytes(g.B);
+  const size_t smem3 = smem1 + (size_t)ZW * z_out_words(g.B) * 4;
+  static bool configured[64] = {false};   // the largest B's sizes, once per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 64 || !configured[dev]) {
+    const int max1 = ZW * z_in_bytes(NUMARCK_MAX_B);
+    const int max3 = max1 + ZW * z_out_words(NUMARCK_MAX_B) * 4;
+    cudaError_t e = cudaFuncSetAttribute(z1_size, cudaFuncAttributeMaxDynamicSharedMemorySize, max1);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(z3_write, cudaFuncAttributeMaxDynamicSharedMemorySize, max3);
+    if (e != cudaSuccess) return e;
+    if (dev < 64) configured[dev] = true;
+  }
   long long blocks = (g.nsub + ZW - 1) / ZW;
   if (blocks > (long long)sms * 32) blocks = (long long)sms * 32;
-  z1_size<<<(int)blocks, ZT, 0, s>>>(A);
+  z1_size<<<(int)blocks, ZT, smem1, s>>>(A);
   z2_scan<<<1, 1024, 0, s>>>(A);
-  z3_write<<<(int)blocks, ZT, 0, s>>>(A);
+  z3_write<<<(int)blocks, ZT, smem3, s>>>(A);
   return cudaGetLastError();
 }
 
