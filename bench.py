@@ -604,6 +604,18 @@ def run_served(args):
     print(json.dumps(line), flush=True)
 
 
+def _host_mem_available():
+    """MemAvailable of this host in bytes (None where /proc/meminfo is missing)."""
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return None
+
+
 def run_e2e(args, xs, n, bound, dist, dev, ws, recon_out=True):
     """End-to-end metric through the public API: host timesteps in, blobs (and reconstructions)
     out, each (E, B) chain as in the device-resident run (compress, two chained steps,
@@ -987,10 +999,21 @@ def main():
     # device->host on their own streams as soon as they are ready
     e2e = e2e_blob = None
     if not args.no_e2e and args.e2e_steps > 0:
-        e2e = run_e2e(args, xs, n, bound, dist, dev, ws)
-        # the same without the reconstruction leaving the device (it is the next prev of the
-        # closed loop, Eq. 4): the blobs and the decode status are the step's results
-        e2e_blob = run_e2e(args, xs, n, bound, dist, dev, ws, recon_out=False)
+        # host memory per rank: the 4 timesteps, a blob and a reconstruction pinned, plus one
+        # pageable timestep while pinning; every rank of the node holds its own
+        local_ranks = int(os.environ.get("LOCAL_WORLD_SIZE", "1"))
+        need = local_ranks * (6 * n * L + bound)
+        avail = _host_mem_available()
+        if avail is not None and need > 0.8 * avail:
+            why = (f"skipped: the end-to-end run pins {need / 1e9:.0f} GB of host memory on this "
+                   f"node ({local_ranks} ranks) and {avail / 1e9:.0f} GB are available")
+            e2e = {"value": None, "unit": "GB/s", "note": why}
+            e2e_blob = {"value": None, "unit": "GB/s", "note": why}
+        else:
+            e2e = run_e2e(args, xs, n, bound, dist, dev, ws)
+            # the same without the reconstruction leaving the device (it is the next prev of the
+            # closed loop, Eq. 4): the blobs and the decode status are the step's results
+            e2e_blob = run_e2e(args, xs, n, bound, dist, dev, ws, recon_out=False)
 
     # quality of every pair of the step, from one more run of each chain (outside the timed
     # region): CR (Eq. 2, raw blob), ME (Eq. 3), the largest relative error, and the points
