@@ -354,3 +354,37 @@ def test_auto_B_refused_while_capturing():
                                       blob.data_ptr(), blob.numel(), ws.data_ptr(), ws.numel(),
                                       s.cuda_stream)
     assert rc == N.ERR_INVALID_ARG
+
+
+def test_corrupted_offset_tables_are_reported():
+    """A blob whose offset tables disagree with its index table is refused through the status
+    word, by the decoder and by the chained step (whose next blob then carries the error)."""
+    p, x = synth.plain_pair(200_000, seed=synth.seed_for(0, 95))
+    y, _ = synth.plain_pair(200_000, seed=synth.seed_for(0, 96))
+    pd, xd, yd = p.to(DEV), x.to(DEV), y.to(DEV)
+    blob = N.compress(pd, xd, 1e-3, 8)
+    torch.cuda.synchronize()
+    h = N.parse_header(N.header_bytes(blob))
+    assert h["nsub"] > 8
+    for field, idx, how in (("off_sub_off", 5, lambda v: v + 3),
+                            ("off_sub_off", 7, lambda v: -10 ** 9),
+                            ("off_sub_off", 2, lambda v: h["n_inc"] + 1),
+                            ("off_idx_off", 0, lambda v: v + 16)):
+        bad = blob.clone()
+        at = h[field] + 8 * idx
+        word = bad[at: at + 8].view(torch.int64)
+        word.copy_(torch.tensor([how(int(word.item()))], dtype=torch.int64, device=DEV))
+        status = torch.zeros(1, dtype=torch.int32, device=DEV)
+        N.decompress(bad, pd, status=status)
+        torch.cuda.synchronize()
+        assert int(status.item()) == N.ERR_CORRUPT, (field, idx)
+        status.zero_()
+        _, nxt = N.decompress_compress(bad, pd, yd, 1e-3, 8, status=status)
+        torch.cuda.synchronize()
+        assert int(status.item()) == N.ERR_CORRUPT, (field, idx)
+        assert N.parse_header(N.header_bytes(nxt))["status"] == N.ERR_CORRUPT
+    # the intact blob still decodes
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    N.decompress(blob, pd, status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
