@@ -133,4 +133,52 @@ __device__ __forceinline__ unsigned markers_before(const unsigned* tw, int tword
   return __reduce_add_sync(0xffffffffu, c);
 }
 
+// One 128-point step of a decode, lane l holding points e0 .. e0+3 (e0 = step start + 4l): their
+// indices from the lane's 4B-bit field, the step's incompressible points numbered in element
+// order across the warp (four ballots: the lanes before this one, then this lane's earlier
+// points) from position `run` of the incompressible table, and r[k] = prev * m[idx] (Eq. 4) or
+// the stored value. Points at or past cnt are not counted. An incompressible point whose
+// position lies past n_inc reads 0 and, when it lies in [e_lo, e_hi), reports corruption.
+// Returns the step's count of incompressible points (the same in every lane).
+template <typename T, int B>
+__device__ __forceinline__ unsigned decode_step(typename Field<B>::type field, const T (&pv)[4],
+                                                int e0, int cnt, int e_lo, int e_hi,
+                                                long long run, unsigned lt, const T* s_m,
+                                                const T* centres,
+                                                const typename BitsOf<T>::U* exact_u,
+                                                long long n_inc, const DecodeArgs& A, T (&r)[4]) {
+  using U = typename BitsOf<T>::U;
+  constexpr unsigned M = (1u << B) - 1u;
+  unsigned id[4];
+  unsigned nib = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    id[k] = (unsigned)(field >> (k * B)) & M;
+    nib |= (e0 + k < cnt && id[k] == M) ? (1u << k) : 0u;
+  }
+  unsigned before = 0, total = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const unsigned bk = __ballot_sync(0xffffffffu, (nib >> k) & 1u);
+    before += __popc(bk & lt);
+    total += __popc(bk);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if ((nib >> k) & 1u) {
+      const long long pos = run + before + __popc(nib & ((1u << k) - 1u));
+      U v = 0;
+      if (pos < n_inc) v = exact_u[pos];
+      else if (e0 + k >= e_lo && e0 + k < e_hi) report(A, NUMARCK_ERR_CORRUPT);
+      r[k] = BitsOf<T>::as(v);
+    } else {
+      T m;
+      if constexpr ((1 << B) <= DM_SMEM) m = s_m[id[k]];
+      else m = id[k] < (unsigned)DM_SMEM ? s_m[id[k]] : t_add((T)1, centres[id[k]]);
+      r[k] = t_mul(pv[k], m);
+    }
+  }
+  return total;
+}
+
 }  // namespace nmk

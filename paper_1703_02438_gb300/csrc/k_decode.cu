@@ -33,7 +33,6 @@ __device__ __forceinline__ void decode_tiles(const DecodeArgs& A, const Geometry
   using U = typename BitsOf<T>::U;
   using F = typename Field<B>::type;
   constexpr int FB = 4 * B;
-  constexpr unsigned M = (1u << B) - 1u;
   const int lane = (int)lane_id();
   const int warp = (int)(threadIdx.x >> 5);
   const T* centres = reinterpret_cast<const T*>(A.blob + g.off_centres);
@@ -99,39 +98,9 @@ __device__ __forceinline__ void decode_tiles(const DecodeArgs& A, const Geometry
         const int sb0 = s0 + u * K4_SEG;
         if (sb0 >= send) break;                  // uniform across the warp
         const int e0 = sb0 + 4 * lane;
-        unsigned id[4];
-        unsigned nib = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          id[k] = (unsigned)(field[u] >> (k * B)) & M;
-          nib |= (e0 + k < cnt && id[k] == M) ? (1u << k) : 0u;
-        }
-        // element-order numbering of the step's incompressible points: lanes before this one,
-        // then this lane's earlier elements
-        unsigned before = 0, total = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const unsigned bk = __ballot_sync(0xffffffffu, (nib >> k) & 1u);
-          before += __popc(bk & lt);
-          total += __popc(bk);
-        }
         T r[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          if ((nib >> k) & 1u) {
-            const long long pos = run + before + __popc(nib & ((1u << k) - 1u));
-            U v = 0;
-            if (pos < n_inc) v = exact_u[pos];
-            else if (e0 + k >= e_lo && e0 + k < e_hi)
-              report(A, NUMARCK_ERR_CORRUPT);
-            r[k] = BitsOf<T>::as(v);
-          } else {
-            T m;
-            if constexpr ((1 << B) <= DM_SMEM) m = s_m[id[k]];
-            else m = id[k] < (unsigned)DM_SMEM ? s_m[id[k]] : t_add((T)1, centres[id[k]]);
-            r[k] = t_mul(pv[u][k], m);
-          }
-        }
+        const unsigned total = decode_step<T, B>(field[u], pv[u], e0, cnt, e_lo, e_hi, run, lt, s_m,
+                                                 centres, exact_u, n_inc, A, r);
         run += total;
         if (vec && sb0 + K4_SEG <= e_hi) {
           st4(ot + e0, r);

@@ -43,7 +43,6 @@ __device__ __forceinline__ void step_tiles(const DecodeArgs& A, const StepArgs& 
   using U = typename BitsOf<T>::U;
   using F = typename Field<B>::type;
   constexpr int FB = 4 * B;
-  constexpr unsigned M = (1u << B) - 1u;
   const int lane = (int)lane_id();
   const int warp = (int)(threadIdx.x >> 5);
   const T* centres = reinterpret_cast<const T*>(A.blob + g.off_centres);
@@ -103,36 +102,9 @@ __device__ __forceinline__ void step_tiles(const DecodeArgs& A, const StepArgs& 
         }
       }
       // decompression of the four points (as K4)
-      unsigned id[4];
-      unsigned nib = 0;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        id[k] = (unsigned)(field >> (k * B)) & M;
-        nib |= (e0 + k < cnt && id[k] == M) ? (1u << k) : 0u;
-      }
-      unsigned before = 0, total = 0;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const unsigned bk = __ballot_sync(0xffffffffu, (nib >> k) & 1u);
-        before += __popc(bk & lt);
-        total += __popc(bk);
-      }
       T r[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if ((nib >> k) & 1u) {
-          const long long pos = run + before + __popc(nib & ((1u << k) - 1u));
-          U v = 0;
-          if (pos < n_inc) v = exact_u[pos];
-          else report(A, NUMARCK_ERR_CORRUPT);
-          r[k] = BitsOf<T>::as(v);
-        } else {
-          T m;
-          if constexpr ((1 << B) <= DM_SMEM) m = s_m[id[k]];
-          else m = id[k] < (unsigned)DM_SMEM ? s_m[id[k]] : t_add((T)1, centres[id[k]]);
-          r[k] = t_mul(pv[k], m);
-        }
-      }
+      const unsigned total = decode_step<T, B>(field, pv, e0, cnt, 0, cnt, run, lt, s_m, centres,
+                                               exact_u, n_inc, A, r);
       run += total;
       if (vec && whole) {
         st4(ot + e0, r);
