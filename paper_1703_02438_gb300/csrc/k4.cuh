@@ -1,6 +1,7 @@
 // k4.cuh — the pieces of K4 (decompression, §III.E with Eq. 4 read as R = prev * (1 + centre))
 // shared by the decode kernel (k_decode.cu) and the fused decompress-and-classify kernel
-// (k_step.cu): vector loads and stores, and the B-bit field of a lane in a 128-element step.
+// (k_step.cu): vector loads and stores, the B-bit field of a lane in a 128-element step, the
+// decode of one step, and the split of a sub-block between warps for small variables.
 #pragma once
 
 #include <type_traits>
@@ -17,7 +18,7 @@ struct DecodeArgs {
   long long start, count, n_expected;
   int* status2;              // a second error word (the next compression's), or null
   int dtype;                 // NUMARCK_F32 / NUMARCK_F64 the blob must hold, or 0 for either
-  int seg_log2;              // each sub-block is decoded by 2^seg_log2 warps (see seg_count)
+  int seg_log2;              // each sub-block is decoded by 2^seg_log2 warps (see seg_log2_for)
 };
 
 // An error found on the device goes to both status words (either may be null).

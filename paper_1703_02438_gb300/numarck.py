@@ -326,6 +326,76 @@ def decompress_compress(blob: torch.Tensor, prev: torch.Tensor, next_cur: torch.
     return out, next_blob
 
 
+class Chain:
+    """A chain of timesteps of one variable compressed as the paper's in-situ use does (Eq. 4:
+    each timestep against the reconstruction of the previous one), through the chained step.
+
+    push(x) takes the next timestep (a 1-D CUDA tensor of the chain's dtype and length). The
+    first push only keeps x as the reference. Every later push returns the blob of x (a view of
+    an internal buffer, valid until the push after next); from the third push on, the
+    reconstruction of the previous timestep is made by the same call that compresses x
+    (numarck_decompress_compress). reconstruction() returns the reconstruction of the latest
+    timestep (decompressing the latest blob if the next push has not made it yet)."""
+
+    def __init__(self, n: int, dtype, E: float, B: int, anchor: int = ANCHOR_ZERO,
+                 block_bytes: int = 0, device="cuda", stream=None):
+        self.n, self.dtype, self.E, self.B = int(n), dtype, float(E), int(B)
+        self.anchor, self.block_bytes, self.stream = anchor, block_bytes, stream
+        params = make_params(dtype, B, E, anchor, block_bytes)
+        bound = compress_bound(self.n, params)
+        if bound == 0:
+            raise NumarckError(ERR_INVALID_ARG, "numarck_compress_bound")
+        dev = torch.device(device)
+        self.blobs = [torch.empty(bound, dtype=torch.uint8, device=dev) for _ in range(2)]
+        self.recs = [torch.empty(self.n, dtype=dtype, device=dev) for _ in range(2)]
+        self.ws = Workspace(dev)
+        self.ws.get(workspace_bytes(self.n, params), stream)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.ref = None          # the first timestep (the prev of the first blob)
+        self.base = None         # the prev the latest blob was compressed against
+        self.latest = -1         # index of the blob buffer holding the latest blob
+        self.recon = None        # reconstruction of the latest timestep, once made
+        self.t = 0               # timesteps pushed
+
+    def push(self, x: torch.Tensor):
+        if x.dtype != self.dtype or x.numel() != self.n or x.dim() != 1 or not x.is_cuda:
+            raise ValueError("a timestep must be a 1-D CUDA tensor of the chain's dtype and length")
+        kw = dict(anchor=self.anchor, block_bytes=self.block_bytes, workspace=self.ws,
+                  stream=self.stream)
+        self.t += 1
+        if self.t == 1:
+            self.ref = x.clone()
+            self.recon = self.ref
+            return None
+        nxt = 0 if self.latest != 0 else 1
+        if self.t == 2:
+            compress(self.ref, x, self.E, self.B, blob=self.blobs[nxt], **kw)
+            self.base = self.ref
+        else:
+            # the reconstruction of the previous timestep, made while compressing x against it
+            out = self._free_rec()
+            decompress_compress(self.blobs[self.latest], self.base, x, self.E, self.B, out=out,
+                                next_blob=self.blobs[nxt], status=self.status, **kw)
+            self.base = out
+        self.latest = nxt
+        self.recon = None
+        return self.blobs[nxt]
+
+    def _free_rec(self) -> torch.Tensor:
+        # the reconstruction buffer that is not the base of the latest blob
+        return self.recs[1] if self.base is self.recs[0] else self.recs[0]
+
+    def reconstruction(self) -> torch.Tensor:
+        if self.recon is None:
+            self.recon = decompress(self.blobs[self.latest], self.base, out=self._free_rec(),
+                                    status=self.status, stream=self.stream)
+        return self.recon
+
+    def check(self) -> int:
+        """The device status word of the chain's decompressions (synchronises)."""
+        return int(self.status.item())
+
+
 def selftest_wait(flag: torch.Tensor, limit_ns: int, status: torch.Tensor, stream=None) -> None:
     """Queues the library's bounded device wait on `flag` (an int64 CUDA tensor): `status`
     (int32 CUDA tensor) receives OK if the flag is non-zero within limit_ns, else ERR_TIMEOUT

@@ -147,3 +147,24 @@ def test_device_error_reaches_the_next_blob():
     sep = _used(N.compress(rec_sep, s[2], 1e-3, 8))
     _, nxt = N.decompress_compress(b1, s[0], s[2], 1e-3, 8)
     assert _used(nxt) == sep
+
+
+@pytest.mark.parametrize("E,B", [(1e-3, 8), (1e-4, 10)])
+def test_chain_helper_matches_oracle(E, B):
+    """numarck.Chain (push one timestep at a time) gives the oracle's chain: every blob byte for
+    byte, and the reconstruction of the latest timestep bit for bit."""
+    s = synth.flash_series(side=64, steps=5, device=DEV, seed=synth.seed_for(1, 120 + B))
+    ch = N.Chain(s[0].numel(), torch.float64, E, B, device=DEV)
+    assert ch.push(s[0]) is None
+    prev_np = s[0].cpu().numpy()
+    for t in range(1, 5):
+        blob = ch.push(s[t])
+        want = O.compress(prev_np, s[t].cpu().numpy(), E, B).to_bytes()
+        assert _used(blob) == want, f"blob {t}"
+        prev_np = O.decompress(want, prev_np)
+        if t == 2:          # an on-demand reconstruction between pushes does not disturb the chain
+            assert np.array_equal(_u(ch.reconstruction().cpu().numpy()), _u(prev_np))
+    rec = ch.reconstruction()
+    torch.cuda.synchronize()
+    assert ch.check() == 0
+    assert np.array_equal(_u(rec.cpu().numpy()), _u(prev_np))
