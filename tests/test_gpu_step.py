@@ -168,3 +168,12 @@ def test_chain_helper_matches_oracle(E, B):
     torch.cuda.synchronize()
     assert ch.check() == 0
     assert np.array_equal(_u(rec.cpu().numpy()), _u(prev_np))
+
+
+def test_empty_step():
+    """n = 0: nothing to decompress; the next blob is the empty compression's."""
+    e = torch.empty(0, dtype=torch.float64, device=DEV)
+    b = N.compress(e, e, 1e-3, 8)
+    rec, nxt = N.decompress_compress(b, e, e, 1e-3, 8)
+    assert rec.numel() == 0
+    assert _used(nxt) == O.compress(np.empty(0), np.empty(0), 1e-3, 8).to_bytes()
