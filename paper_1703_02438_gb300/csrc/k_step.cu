@@ -14,6 +14,15 @@
 //
 // Used for the zero-centred grid only (the paper-literal grid anchored at the minimum ratio
 // needs that minimum over all of R before any bin is known).
+//
+// Each warp works through its sub-block in 128-point steps, and every step would otherwise wait
+// for two round trips to memory: its index field, prev and cur values, then the incompressible
+// values that the field selects. For B <= K41_STAGE_MAX_B the warp instead copies the next
+// step's prev and cur values and its index field into a stage in shared memory (cp.async) before
+// it classifies the current step, so only the second round trip is left. The stages take no
+// registers (K41 is at its register cap; holding the next field in a register cost more than the
+// staging saved), and one 1024-thread CTA per SM keeps 32 warps resident with a single K1 window,
+// which leaves the shared memory for the stages without shrinking the L1 cache.
 #include <algorithm>
 
 #include "k1.cuh"
@@ -23,8 +32,87 @@ namespace nmk {
 
 namespace {
 
-constexpr int K41_WARPS = 16;                    // warps per CTA (each owns a sub-block or a part)
-constexpr int K41_THREADS = K41_WARPS * 32;
+constexpr int K41_WARPS = 32;                    // warps per CTA (each owns a sub-block or a part)
+constexpr int K41_THREADS = K41_WARPS * 32;      // one CTA per SM
+constexpr int K41_STAGE_MAX_B = 10;             // index lengths whose steps are staged
+
+// Shared memory after K1's window. With B <= K41_STAGE_MAX_B: the 2^B multipliers (room for
+// TAB), then one stage per warp: a step's prev values, its cur values and its 16 B bytes of index
+// field. With larger B the region holds the first DM_SMEM multipliers and no step is staged.
+template <typename T>
+struct Stage {
+  static constexpr int L = (int)sizeof(T);
+  static constexpr int FIELD = 2 * K4_SEG * L;   // byte offset of the field in a stage
+  static constexpr int BYTES = FIELD + 16 * K41_STAGE_MAX_B;
+  static constexpr int TAB = 1 << K41_STAGE_MAX_B;
+  static constexpr int REGION = std::max(TAB * L + K41_WARPS * BYTES, DM_SMEM * L);
+};
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n"
+               :: "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void lds4(const double* p, double* v) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0];
+  const double2 b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void lds4(const float* p, float* v) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+
+// Starts the copies of the whole step at s1 (16-byte aligned inputs and tile image tw) into the
+// warp's stage wst: this lane's four prev and four cur values, and (lanes 0 .. B-1) the step's
+// 16 B bytes of index field.
+template <typename T, int B>
+__device__ __forceinline__ void stage_step(unsigned char* wst, const T* pt, const T* xt, int s1,
+                                           int lane, const unsigned* tw) {
+  constexpr int L = Stage<T>::L;
+  T* sp = reinterpret_cast<T*>(wst);
+  T* sc = sp + K4_SEG;
+  const int e = s1 + 4 * lane;
+#pragma unroll
+  for (int c = 0; c < 4 * L / 16; ++c) {
+    cp_async16(sp + 4 * lane + c * (16 / L), pt + e + c * (16 / L));
+    cp_async16(sc + 4 * lane + c * (16 / L), xt + e + c * (16 / L));
+  }
+  if (lane < B)
+    cp_async16(wst + Stage<T>::FIELD + 16 * lane,
+               reinterpret_cast<const unsigned char*>(tw) + (s1 / K4_SEG) * 16 * B + 16 * lane);
+  cp_async_commit();
+}
+
+// load_field for a staged step: the 4B-bit field of lane `lane` from the step's own 4B words.
+template <int B>
+__device__ __forceinline__ typename Field<B>::type load_field_staged(const unsigned* sw, int lane) {
+  constexpr int FB = 4 * B;
+  constexpr int NW = B * 4;                      // words of one step's image
+  using F = typename Field<B>::type;
+  if constexpr (FB == 32) {
+    return sw[lane];
+  } else {
+    static_assert(FB < 64, "staged steps have B <= 10");
+    const int bit = FB * lane;
+    const int w0 = bit >> 5, o = bit & 31;
+    const unsigned a0 = sw[w0];
+    const unsigned a1 = (o + FB > 32 && w0 + 1 < NW) ? sw[w0 + 1] : 0u;
+    const unsigned long long v = (unsigned long long)a0 | ((unsigned long long)a1 << 32);
+    if constexpr (FB > 32) {
+      const unsigned a2 = (o + FB > 64 && w0 + 2 < NW) ? sw[w0 + 2] : 0u;
+      return (F)((v >> o) | (o ? ((unsigned long long)a2 << (64 - o)) : 0ull));
+    } else {
+      return (F)(v >> o);
+    }
+  }
+}
 
 struct StepArgs {
   const void* cur;               // the next timestep, n elements of T
@@ -38,13 +126,17 @@ struct StepArgs {
 template <typename T, int B>
 __device__ __forceinline__ void step_tiles(const DecodeArgs& A, const StepArgs& S,
                                            const Geometry& g, long long n_inc, const T* s_m,
-                                           const Consts<T>& c, const HistCtx& h, int& lmin,
-                                           int& lmax) {
+                                           unsigned char* stages, const Consts<T>& c,
+                                           const HistCtx& h, int& lmin, int& lmax) {
   using U = typename BitsOf<T>::U;
   using F = typename Field<B>::type;
   constexpr int FB = 4 * B;
+  constexpr bool kStage = B <= K41_STAGE_MAX_B;
   const int lane = (int)lane_id();
   const int warp = (int)(threadIdx.x >> 5);
+  unsigned char* wst = stages + warp * Stage<T>::BYTES;
+  const T* sp = reinterpret_cast<const T*>(wst);
+  const unsigned* sw = reinterpret_cast<const unsigned*>(wst + Stage<T>::FIELD);
   const T* centres = reinterpret_cast<const T*>(A.blob + g.off_centres);
   const int64_t* idx_off = reinterpret_cast<const int64_t*>(A.blob + g.off_idx_off);
   const int64_t* sub_off = reinterpret_cast<const int64_t*>(A.blob + g.off_sub_off);
@@ -85,16 +177,26 @@ __device__ __forceinline__ void step_tiles(const DecodeArgs& A, const StepArgs& 
     const bool vec = ((reinterpret_cast<uintptr_t>(pt) | reinterpret_cast<uintptr_t>(ot) |
                        reinterpret_cast<uintptr_t>(xt)) & 15) == 0;
     const bool cvec = (reinterpret_cast<uintptr_t>(ct) & 7) == 0;
+    const bool stage_ok = kStage && vec && (reinterpret_cast<uintptr_t>(tw) & 15) == 0;
     long long run = base + (sbeg ? markers_before<B>(tw, twords, cnt, sbeg, lane) : 0u);
+    bool staged = false;                         // this step's inputs are in the stage
     for (int s0 = sbeg; s0 < send; s0 += K4_SEG) {
       const int e0 = s0 + 4 * lane;
       const bool whole = s0 + K4_SEG <= cnt;     // uniform across the warp
-      const F field = load_field<B>(tw, twords, (s0 / K4_SEG) * FB, lane);
+      F field;
       T pv[4], xv[4];
-      if (vec && whole) {
+      if (staged) {
+        cp_async_wait_all();
+        __syncwarp();                            // the field words other lanes copied
+        if constexpr (kStage) field = load_field_staged<B>(sw, lane);
+        lds4(sp + 4 * lane, pv);
+        lds4(sp + K4_SEG + 4 * lane, xv);
+      } else if (vec && whole) {
+        field = load_field<B>(tw, twords, (s0 / K4_SEG) * FB, lane);
         ld4(pt + e0, pv);
         ld4(xt + e0, xv);
       } else {
+        field = load_field<B>(tw, twords, (s0 / K4_SEG) * FB, lane);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           pv[k] = e0 + k < cnt ? __ldcs(pt + e0 + k) : (T)0;
@@ -106,6 +208,16 @@ __device__ __forceinline__ void step_tiles(const DecodeArgs& A, const StepArgs& 
       const unsigned total = decode_step<T, B>(field, pv, e0, cnt, 0, cnt, run, lt, s_m, centres,
                                                exact_u, n_inc, A, r);
       run += total;
+      // the next step's inputs, in flight while this step is classified
+      staged = false;
+      if constexpr (kStage) {
+        const int s1 = s0 + K4_SEG;
+        if (stage_ok && s1 < send && s1 + K4_SEG <= cnt) {
+          __syncwarp();                          // every lane has read this step's field
+          stage_step<T, B>(wst, pt, xt, s1, lane, tw);
+          staged = true;
+        }
+      }
       if (vec && whole) {
         st4(ot + e0, r);
       } else {
@@ -157,20 +269,20 @@ __device__ __forceinline__ void step_tiles(const DecodeArgs& A, const StepArgs& 
 template <typename T, int B = 1>
 __device__ __forceinline__ void step_dispatch(const DecodeArgs& A, const StepArgs& S,
                                               const Geometry& g, long long n_inc, const T* s_m,
-                                              const Consts<T>& c, const HistCtx& h, int& lmin,
-                                              int& lmax) {
+                                              unsigned char* stages, const Consts<T>& c,
+                                              const HistCtx& h, int& lmin, int& lmax) {
   if constexpr (B <= NUMARCK_MAX_B) {
     if (g.B == B)
-      step_tiles<T, B>(A, S, g, n_inc, s_m, c, h, lmin, lmax);
+      step_tiles<T, B>(A, S, g, n_inc, s_m, stages, c, h, lmin, lmax);
     else
-      step_dispatch<T, B + 1>(A, S, g, n_inc, s_m, c, h, lmin, lmax);
+      step_dispatch<T, B + 1>(A, S, g, n_inc, s_m, stages, c, h, lmin, lmax);
   }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(K41_THREADS, 2) k41_step(DecodeArgs A, StepArgs S, Consts<T> c) {
-  extern __shared__ unsigned int sh[];                           // K1's shared window
-  __shared__ __align__(16) unsigned char s_tab[DM_SMEM * 8];     // multipliers m = 1 + centre
+__global__ void __launch_bounds__(K41_THREADS, 1) k41_step(DecodeArgs A, StepArgs S, Consts<T> c) {
+  extern __shared__ __align__(16) unsigned int sh[];             // K1's shared window, then
+  unsigned char* region = reinterpret_cast<unsigned char*>(sh + SH_BINS);   // Stage's region
   __shared__ __align__(16) numarck_header s_h;
   __shared__ Geometry s_g;
   __shared__ int s_rc;
@@ -199,12 +311,13 @@ __global__ void __launch_bounds__(K41_THREADS, 2) k41_step(DecodeArgs A, StepArg
       codes[j] = (unsigned short)CODE_NONE;
   } else {
     const Geometry g = s_g;
-    const int nm = min(1 << g.B, DM_SMEM);
-    T* s_m = reinterpret_cast<T*>(s_tab);
+    const int nm = min(1 << g.B, DM_SMEM);      // within TAB when B <= K41_STAGE_MAX_B
+    T* s_m = reinterpret_cast<T*>(region);
     const T* centres = reinterpret_cast<const T*>(A.blob + g.off_centres);
     for (int r = threadIdx.x; r < nm; r += K41_THREADS) s_m[r] = t_add((T)1, centres[r]);
     __syncthreads();
-    step_dispatch<T>(A, S, g, s_h.n_inc, s_m, c, h, lmin, lmax);
+    step_dispatch<T>(A, S, g, s_h.n_inc, s_m, region + Stage<T>::TAB * sizeof(T), c, h, lmin,
+                     lmax);
   }
   k1_end(h, lmin, lmax);
 }
@@ -214,7 +327,7 @@ cudaError_t launch_step_t(const DecodePlan& D, const CompressPlan& P, cudaStream
   static int occ[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
-  const size_t smem = SH_BINS * sizeof(unsigned int);
+  const size_t smem = SH_BINS * sizeof(unsigned int) + Stage<T>::REGION;
   int per_sm = dev < 64 ? occ[dev] : 0;
   if (per_sm == 0) {
     cudaError_t e = cudaFuncSetAttribute(k41_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
