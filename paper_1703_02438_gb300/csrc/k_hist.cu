@@ -12,6 +12,11 @@
 // zero-change bin (one shared atomic per point), and each CTA merges its window into the
 // global histogram once at the end.
 // Bins outside the shared window go straight to the global window with one atomic.
+//
+// One CTA of 32 warps per SM. With 16-byte aligned inputs each warp copies its next step's prev
+// and cur vectors into its stage in shared memory (cp.async) before it classifies the current
+// step, so its loads stay in flight while it computes (the kernel is at its register cap: a
+// second register group of inputs spilled).
 #include "k1.cuh"
 
 namespace nmk {
@@ -58,17 +63,29 @@ __global__ void __launch_bounds__(512) k0_anchor_min(const T* __restrict__ prev,
 // ---------------------------------------------------------------------------------------
 // K1
 // ---------------------------------------------------------------------------------------
-constexpr int K1_THREADS = 512;
-constexpr int K1_UNROLL = 4;
+constexpr int K1_THREADS = 1024;                // one CTA per SM
+constexpr int K1_UNROLL = 2;                    // 16-byte vectors of each input per lane per step
+constexpr int K1_STAGE = 2 * K1_UNROLL * 32 * 16;   // bytes of a warp's stage (prev, cur)
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n"
+               :: "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
 
 template <typename T, bool VEC>
-__global__ void __launch_bounds__(K1_THREADS, 2) k1_hist(const T* __restrict__ prev,
+__global__ void __launch_bounds__(K1_THREADS, 1) k1_hist(const T* __restrict__ prev,
                                                       const T* __restrict__ cur, int64_t n,
                                                       Consts<T> c, int anchor_min, Ctrl* ctrl,
                                                       unsigned long long* hist,
                                                       unsigned long long* tstatus, int64_t nsub,
                                                       unsigned short* codes) {
-  extern __shared__ unsigned int sh[];
+  extern __shared__ __align__(16) unsigned int sh[];   // K1's window, then the warps' stages
   if (anchor_min) anchor_min_consts<T>(c, ctrl);
   int c0 = 0;  // bin of a zero change ratio: centre of the shared window
   if (anchor_min) {
@@ -89,18 +106,38 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_hist(const T* __restrict__ p
     const VT* pv = reinterpret_cast<const VT*>(prev);
     const VT* xv = reinterpret_cast<const VT*>(cur);
     const int64_t nvec = n / V::N;
-    for (int64_t base = gwarp * (32 * K1_UNROLL); base < nvec; base += nwarps * (32 * K1_UNROLL)) {
+    // this lane's slots of the warp's stage: [u][lane] prev vectors, then cur vectors; a lane
+    // reads back only what it copied itself
+    VT* sp = reinterpret_cast<VT*>(reinterpret_cast<unsigned char*>(sh + SH_BINS) +
+                                   (threadIdx.x >> 5) * K1_STAGE);
+    VT* sx = sp + K1_UNROLL * 32;
+    const int64_t step = nwarps * (32 * K1_UNROLL);
+    auto stage = [&](int64_t b0) {
+#pragma unroll
+      for (int u = 0; u < K1_UNROLL; ++u) {
+        const int64_t vi = b0 + u * 32 + lane;
+        if (vi < nvec) {
+          cp_async16(sp + u * 32 + lane, pv + vi);
+          cp_async16(sx + u * 32 + lane, xv + vi);
+        }
+      }
+      cp_async_commit();
+    };
+    if (gwarp * (32 * K1_UNROLL) < nvec) stage(gwarp * (32 * K1_UNROLL));
+    for (int64_t base = gwarp * (32 * K1_UNROLL); base < nvec; base += step) {
       T pe[K1_UNROLL][V::N], xe[K1_UNROLL][V::N];
       bool ok[K1_UNROLL];
+      cp_async_wait_all();
 #pragma unroll
       for (int u = 0; u < K1_UNROLL; ++u) {
         const int64_t vi = base + u * 32 + lane;
         ok[u] = vi < nvec;
         VT a = {}, b = {};
-        if (ok[u]) { a = __ldcs(pv + vi); b = __ldcs(xv + vi); }
+        if (ok[u]) { a = sp[u * 32 + lane]; b = sx[u * 32 + lane]; }
         V::get(a, pe[u]);
         V::get(b, xe[u]);
       }
+      if (base + step < nvec) stage(base + step);   // in flight while this step is classified
       unsigned pend = 0;   // bit u * V::N + v: element needs the exact sequences
 #pragma unroll
       for (int u = 0; u < K1_UNROLL; ++u) {
@@ -200,7 +237,7 @@ cudaError_t launch_hist_tv(const CompressPlan& P, cudaStream_t s) {
   static int occ[64] = {0};   // resident CTAs per SM, per device (0 = not configured yet)
   int dev = 0;
   cudaGetDevice(&dev);
-  const size_t smem = SH_BINS * sizeof(unsigned int);
+  const size_t smem = SH_BINS * sizeof(unsigned int) + (VEC ? (K1_THREADS / 32) * K1_STAGE : 0);
   int per_sm = dev < 64 ? occ[dev] : 0;
   if (per_sm == 0) {
     cudaError_t e = cudaFuncSetAttribute(k1_hist<T, VEC>,
