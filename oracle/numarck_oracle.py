@@ -21,7 +21,7 @@ Readings of the paper where it is silent, ambiguous or garbled (each is used bel
       is incompressible. A ratio with |ratio| > cap = 2^21 * 2E is not binnable either
       (it keeps every bin id inside a 2^22-bin window).
   R2  grid anchor: ZERO (a = -E, default: bin 0 is centred on ratio 0) or MIN (a = the
-      minimum binnable ratio, 0 when there is none).
+      minimum binnable ratio, 0 when there is none; a zero minimum is +0, never -0).
   R3  bin id = floor((ratio - a) * (1 / (2E))), all in T.
   R4  the histogram counts every binnable point.
   R5  k = 2^B - 1 bins; ties in count go to the smaller bin id; selected bins are numbered
@@ -109,7 +109,10 @@ def grid_anchor(ratio: np.ndarray, binnable: np.ndarray, E_T, anchor: int):
     if anchor == ANCHOR_MIN:
         if not binnable.any():
             return T(0)
-        return T(ratio[binnable].min())
+        a = T(ratio[binnable].min())
+        # An unchanged point with a negative prev has ratio +0 / (-p) = -0; reading R2 takes a
+        # zero minimum as +0 whichever signed zero the minimum search meets first.
+        return T(0) if a == 0 else a
     raise ValueError("anchor must be 0 (ZERO) or 1 (MIN)")
 
 

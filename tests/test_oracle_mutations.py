@@ -18,6 +18,7 @@ PINS = [
     lambda: P.test_bin_ids_dyadic_centres_and_edges(np.float64),
     P.test_bin_ids_monotone_in_ratio,
     P.test_min_anchor_puts_minimum_in_bin_zero,
+    P.test_min_anchor_zero_minimum_is_positive_zero,
     P.test_histogram_hand_counted,
     P.test_top_k_matches_brute_force,
     P.test_top_k_fewer_bins_than_k_selects_all,
@@ -80,6 +81,13 @@ def _bins_anchor_sign(ratio, binnable, a, inv_w):
     b = np.zeros(ratio.shape, dtype=np.int64)
     b[binnable] = np.floor(u[binnable]).astype(np.int64)
     return b
+
+
+def _anchor_keeps_signed_zero(ratio, binnable, E_T, anchor):
+    T = type(E_T)
+    if anchor == O.ANCHOR_ZERO:
+        return T(-E_T)
+    return T(ratio[binnable].min()) if binnable.any() else T(0)
 
 
 def _topk_ties_to_larger(bins, counts, k):
@@ -169,6 +177,7 @@ MUTATIONS = {
     "ratio sign flipped": ("change_ratio", _ratio_wrong_sign),
     "bin rounds instead of floor": ("bin_ids", _bins_round),
     "anchor added instead of subtracted": ("bin_ids", _bins_anchor_sign),
+    "zero minimum anchor kept as -0": ("grid_anchor", _anchor_keeps_signed_zero),
     "ties go to the larger bin": ("top_k", _topk_ties_to_larger),
     "indices in count order": ("top_k", _topk_count_order),
     "centre without the half bin": ("centres_of", _centres_no_half),

@@ -140,6 +140,28 @@ def test_min_anchor_puts_minimum_in_bin_zero():
     assert O.grid_anchor(r, ok, E_T, O.ANCHOR_ZERO) == -E_T
 
 
+def test_min_anchor_zero_minimum_is_positive_zero():
+    """Reading R2: a zero minimum ratio is taken as +0. An unchanged point with a negative prev
+    has ratio (x - p) / p = +0 / (-1) = -0, so the raw minimum can be -0; the grid origin, and
+    the header's `a` field written from it, must still be +0 (sign bit clear)."""
+    for T in (np.float32, np.float64):
+        for prev, cur in (([-1.0], [-1.0]),                     # only a -0 ratio
+                          ([2.0, -1.0], [2.0, -1.0]),           # +0 then -0
+                          ([-1.0, 2.0], [-1.0, 2.0]),           # -0 then +0
+                          ([1.0, -1.0, 1.0], [1.5, -1.0, 1.5])):
+            p = np.array(prev, dtype=T)
+            x = np.array(cur, dtype=T)
+            E_T, w, inv_w, cap = O.grid_constants(T, 1e-3)
+            r, ok = O.change_ratio(p, x, cap)
+            a = O.grid_anchor(r, ok, E_T, O.ANCHOR_MIN)
+            assert a == 0 and not np.signbit(a), (T, prev, cur)
+            blob = O.compress(p, x, 1e-3, 8, anchor=O.ANCHOR_MIN)
+            h = O.parse_header(blob.to_bytes())
+            assert h["a"] == 0.0 and not np.signbit(h["a"])
+            # the unchanged points sit in bin 0, whose centre is +E (0 + 0.5 * 2E)
+            assert blob.centres[0] == T(0.5) * w
+
+
 # ---------------------------------------------------------------------------------------
 # Step 3b: histogram, hand counted
 # ---------------------------------------------------------------------------------------
