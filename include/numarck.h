@@ -183,7 +183,9 @@ size_t numarck_workspace_bytes(int64_t n, const numarck_params* p);
 
 /* Zero-fills a workspace (asynchronous on stream). A workspace must be zero-filled once
  * before its first use; every later numarck_compress call leaves it ready for the next
- * one, so it is initialised once and reused. Returns NUMARCK_ERR_INVALID_ARG for a NULL
+ * one, so it is initialised once and reused. That holds for a call whose kernels report an
+ * error in the blob's status word too; only a call that returns NUMARCK_ERR_CUDA (a kernel
+ * that could not be queued) may leave it partly filled, and it is then zero-filled again. Returns NUMARCK_ERR_INVALID_ARG for a NULL
  * pointer, NUMARCK_ERR_CUDA if the memset cannot be queued. */
 int numarck_workspace_init(void* ws, size_t ws_bytes, numarck_stream_t stream);
 

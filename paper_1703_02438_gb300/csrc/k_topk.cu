@@ -251,7 +251,16 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_topk(TopkArgs A, Consts<T> c
   int R = bmax - bmin + 1;
   const int i0 = bmin - c.hbase;
   int status = 0;
-  if (any && (i0 < 0 || i0 + R > HWIN || ctrl->win_err)) { status = NUMARCK_ERR_CORRUPT; R = 0; }
+  // On a window error the selection is skipped (R = 0), but K1 has still counted the bins that
+  // fell inside the window: [clr_lo, clr_hi) is that range, cleared below so that a failed call
+  // leaves the workspace ready like any other.
+  int clr_lo = 0, clr_hi = 0;
+  if (any && (i0 < 0 || i0 + R > HWIN || ctrl->win_err)) {
+    status = NUMARCK_ERR_CORRUPT;
+    clr_lo = i0 > 0 ? i0 : 0;
+    clr_hi = bmax - c.hbase + 1 < HWIN ? bmax - c.hbase + 1 : HWIN;
+    R = 0;
+  }
   // an error of the decompression that made this compression's prev (fused step) marks the blob
   if (ctrl->error) status = ctrl->error;
   unsigned long long* H = A.hist + (any ? i0 : 0);
@@ -329,6 +338,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_topk(TopkArgs A, Consts<T> c
 
   // restore the zero state of the histogram range and the keys
   for (int i = tid; i < R; i += K2_THREADS) H[i] = 0ull;
+  for (int i = clr_lo + tid; i < clr_hi; i += K2_THREADS) A.hist[i] = 0ull;
 
   // blob: idx_off (closed form), the zero gaps between sections, the header
   int64_t* idx_off = reinterpret_cast<int64_t*>(A.blob + g.off_idx_off);

@@ -241,6 +241,58 @@ def test_repeatable_and_workspace_reuse():
     assert first == second
 
 
+@pytest.mark.parametrize("T", [np.float32, np.float64])
+def test_min_anchor_negative_zero_minimum(T):
+    """Reading R2 on the MIN grid: an unchanged point with a negative prev has ratio -0, so the
+    smallest binnable ratio can be -0; the grid origin (and the header's `a`) is +0."""
+    cases = [([2.0, -1.0], [2.0, -1.0]), ([-1.0, 2.0], [-1.0, 2.0]), ([-3.0], [-3.0]),
+             ([1.0, -1.0, 1.0], [1.5, -1.0, 1.5])]
+    rng = np.random.default_rng(61)
+    n = 100_003
+    p = rng.lognormal(size=n) * rng.choice([-1.0, 1.0], n)
+    x = p * (1.0 + rng.uniform(0.0, 0.02, n))      # every ratio >= 0 ...
+    keep = rng.random(n) < 0.3
+    x[keep] = p[keep]                              # ... and 30% unchanged: +0 or -0
+    cases.append((p, x))
+    for prev, cur in cases:
+        h, _ = check_pair(np.array(prev, dtype=T), np.array(cur, dtype=T), 1e-3, 8,
+                          anchor=N.ANCHOR_MIN)
+        assert h["a"] == 0.0 and not np.signbit(h["a"])
+
+
+# byte offset of the window-error flag in the workspace's 256-byte control block (the
+# library's internal layout: 4 + 4 + 8 + 4 + 4 + 6 * 4 bytes of counters, then the anchor
+# as a double at 48, then this flag)
+_CTRL_WIN_ERR = 56
+
+
+def test_workspace_ready_after_device_reported_error():
+    """A compression whose kernels report an error (here a histogram-window error, planted in
+    the workspace's control block) marks its blob and still leaves the workspace ready: the
+    next compression on the same workspace equals the oracle's."""
+    ws = N.Workspace(DEV)
+    rng = np.random.default_rng(62)
+    n = 200_000
+    pa = rng.lognormal(size=n)
+    xa = pa * (1.0 + 0.3 + rng.uniform(-0.01, 0.01, n))   # ratios around 0.3: bins ~150
+    pb, xb = synth.plain_pair(n, seed=synth.seed_for(0, 63))
+    pb, xb = pb.numpy(), xb.numpy()
+    pad, xad = torch.from_numpy(pa).to(DEV), torch.from_numpy(xa).to(DEV)
+    pbd, xbd = torch.from_numpy(pb).to(DEV), torch.from_numpy(xb).to(DEV)
+    N.compress(pbd, xbd, 1e-3, 8, workspace=ws)            # initialises the workspace
+    torch.cuda.synchronize()
+    for anchor in (N.ANCHOR_ZERO, N.ANCHOR_MIN):
+        ws.buf[_CTRL_WIN_ERR:_CTRL_WIN_ERR + 4].view(torch.int32).fill_(1)
+        bad = N.compress(pad, xad, 1e-3, 8, anchor=anchor, workspace=ws)
+        torch.cuda.synchronize()
+        assert N.parse_header(N.header_bytes(bad))["status"] == N.ERR_CORRUPT
+        want = O.compress(pb, xb, 1e-3, 8).to_bytes()
+        blob = N.compress(pbd, xbd, 1e-3, 8, workspace=ws)
+        torch.cuda.synchronize()
+        got = blob[:len(want)].cpu().numpy().tobytes()
+        assert got == want, _first_diff(got, want)
+
+
 def _fraction_pair(n, frac, T, seed):
     """A pair whose incompressible fraction is close to `frac` at E = 1e-4, B = 4: the bulk
     moves by a ratio inside two bins, the chosen fraction by ratios spread over thousands."""
