@@ -255,7 +255,8 @@ def run_reference(args):
 # ----------------------------------------------------------------------------------------
 def run_batched(args):
     """256 variables (sizes log-uniform in [1e4, 2e8], float32/float64, per-variable E and B):
-    per-variable launches on one stream vs one autotuned batch captured in a CUDA graph."""
+    per-variable launches on one stream vs the autotuned lane batch and the autotuned fused
+    batch (one launch per phase over all variables), each captured in a CUDA graph."""
     import torch
     from paper_1703_02438_gb300 import autotune
     from paper_1703_02438_gb300 import build as nbuild
@@ -301,38 +302,62 @@ def run_batched(args):
         plain_decompress()
     t_pc = timed(plain_compress, reps)
     t_pd = timed(plain_decompress, reps)
-    lanes, share, tune_ms = autotune.tune(batch, reps=1, use_cache=False)
-    batch.run()
-    N.decompress_batch(batch.blobs, prevs, outs=outs, lanes=lanes, grid_share=share)
-    torch.cuda.synchronize()
-    gc, gd = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
-    cs = torch.cuda.Stream()
-    cs.wait_stream(stream)
-    with torch.cuda.stream(cs):
-        with torch.cuda.graph(gc, stream=cs):
-            batch.run()
-        with torch.cuda.graph(gd, stream=cs):
-            N.decompress_batch(batch.blobs, prevs, outs=outs, lanes=lanes, grid_share=share)
-    torch.cuda.synchronize()
-    t_bc = timed(gc.replay, reps)
-    t_bd = timed(gd.replay, reps)
+    best, tune_ms = autotune.tune(batch, reps=1, use_cache=False)
+
+    def graphed(key):
+        """Compression and decompression graphs of the batch in configuration `key`."""
+        kind, rest = key.split(":")
+        vals = [int(v) for v in rest.split("x")]
+        if kind == "lanes":
+            batch.set_lanes(*vals)
+        else:
+            batch.set_fused(tuple(vals))
+        batch.run()
+        batch.decompress(prevs, outs=outs)
+        torch.cuda.synchronize()
+        gc, gd = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+        cs = torch.cuda.Stream()
+        cs.wait_stream(stream)
+        with torch.cuda.stream(cs):
+            with torch.cuda.graph(gc, stream=cs):
+                batch.run()
+            with torch.cuda.graph(gd, stream=cs):
+                batch.decompress(prevs, outs=outs)
+        torch.cuda.synchronize()
+        for _ in range(args.warmup):
+            gc.replay()
+            gd.replay()
+        t_c, t_d = timed(gc.replay, reps), timed(gd.replay, reps)
+        return {"config": key, "compress_ms": t_c, "decompress_ms": t_d,
+                "value": nbytes / ((t_c + t_d) / 1e3) / 1e9,
+                "compress_gbs": nbytes / (t_c / 1e3) / 1e9,
+                "decompress_gbs": nbytes / (t_d / 1e3) / 1e9}
+
+    best_of = {kind: min((k for k in tune_ms if k.startswith(kind)), key=tune_ms.get)
+               for kind in ("lanes", "fused")}
+    res = {kind: graphed(k) for kind, k in best_of.items()}
+    # the fused batch's output equals the single calls (checked by the tests); here a spot check
+    # that the timed configuration produced complete blobs
+    for b in batch.blobs[:4]:
+        N.blob_size(N.header_bytes(b))
+    top = max(res.values(), key=lambda r: r["value"])
     sizes = [n for n, *_ in specs]
     line = {"metric": "batched compress+decompress input GB/s (graph-captured batch vs "
                       "per-variable launches)",
-            "value": nbytes / ((t_bc + t_bd) / 1e3) / 1e9, "unit": "GB/s", "n_gpus": 1,
+            "value": top["value"], "unit": "GB/s", "n_gpus": 1,
             "steps": reps, "warmup": args.warmup, "higher_is_better": True, "data": "synthetic",
             "config": {"workload": f"{len(specs)} variables, n log-uniform [1e4, 2e8] "
                                    f"(total {sum(sizes)} elements, {nbytes / 1e9:.1f} GB), "
                                    "float32/float64 50/50, E in {1e-2,1e-3,1e-4}, B in {6,8,10}",
-                       "lanes": lanes, "grid_share": share},
-            "batched": {"compress_ms": t_bc, "decompress_ms": t_bd,
-                        "compress_gbs": nbytes / (t_bc / 1e3) / 1e9,
-                        "decompress_gbs": nbytes / (t_bd / 1e3) / 1e9},
+                       "best": top["config"]},
+            "fused": res["fused"], "lanes": res["lanes"],
             "per_variable": {"compress_ms": t_pc, "decompress_ms": t_pd,
                              "value": nbytes / ((t_pc + t_pd) / 1e3) / 1e9,
                              "compress_gbs": nbytes / (t_pc / 1e3) / 1e9,
                              "decompress_gbs": nbytes / (t_pd / 1e3) / 1e9},
-            "speedup": (t_pc + t_pd) / (t_bc + t_bd), "autotune_ms": tune_ms}
+            "speedup_vs_per_variable": (t_pc + t_pd) / (top["compress_ms"] + top["decompress_ms"]),
+            "fused_vs_lanes": res["lanes"]["value"] and res["fused"]["value"] / res["lanes"]["value"],
+            "autotune_ms": tune_ms}
     print(json.dumps(line), flush=True)
 
 

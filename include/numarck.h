@@ -346,7 +346,9 @@ typedef struct numarck_batch_decode_item {
 size_t numarck_batch_workspace_bytes(const numarck_batch_item* items, int count, int lanes);
 
 /* Compresses count variables. ws: device workspace of >= numarck_batch_workspace_bytes bytes,
- * zero-filled before first use (numarck_workspace_init) and reusable. lanes >= 1 (clamped to
+ * zero-filled before first use (numarck_workspace_init) and reusable with the same item list
+ * and lane count (each lane's slice sits at an offset that depends on both: after a change,
+ * zero-fill it again). lanes >= 1 (clamped to
  * count and 64), grid_share >= 1. Every item is validated on the host before any launch; the
  * return value is the first item error found (nothing is queued then), else NUMARCK_OK. */
 int numarck_compress_batch(const numarck_batch_item* items, int count, int lanes, int grid_share,
@@ -357,6 +359,68 @@ int numarck_compress_batch(const numarck_batch_item* items, int count, int lanes
 int numarck_decompress_batch(const numarck_batch_decode_item* items, int count, int lanes,
                              int grid_share, int32_t* status_dev, numarck_stream_t stream);
 
+/* ---- fused batches (one persistent launch per phase over all variables) ----
+ * The same results as numarck_compress_batch / numarck_decompress_batch (byte for byte the
+ * single-variable results), computed differently: instead of each variable's kernels, every
+ * phase of the method runs as ONE launch over a work list held in device memory that
+ * concatenates all variables' items (their bytes for the ratio/histogram pass of §III.A and
+ * §IV.B.1, one CTA per variable for the top-k selection, their 4096-element tiles for indexing
+ * and packing (§III.C, §IV.C) and for the incompressible copy, their scan blocks for the offset
+ * tables). Each item's dtype, E, B, anchor and block size come from its variable's descriptor.
+ * Every launch fills the GPU regardless of how the batch's sizes are distributed, and a batch
+ * is seven launches per group (plus small upload launches) whatever its count.
+ *
+ * Tuning (NULL: the defaults): k1_threads 512 or 1024 (threads per CTA of the ratio/histogram
+ * pass; 0 = 1024), exact_warps 4 or 8 (warps per CTA of the incompressible copy; 0 = 8),
+ * decode_seg_log2 0..3 (each 4096-element tile is decoded by 2^decode_seg_log2 warps), groups
+ * 1..64 and streams 1..8 (0 = 1 each): the variables are split into `groups` work lists of
+ * about equal bytes, each compressed by its own sequence of fused launches, and the groups run
+ * on `streams` streams of the library (forked from and joined back into the caller's stream)
+ * with every launch sized for 1/streams of the GPU, so that the ALU-bound ratio pass of one group
+ * overlaps the memory-bound passes of another. reserved must be 0. The result does not depend
+ * on the tuning. */
+typedef struct numarck_fused_tuning {
+  int32_t k1_threads;
+  int32_t exact_warps;
+  int32_t decode_seg_log2;
+  int32_t groups;
+  int32_t streams;
+  int32_t reserved;
+} numarck_fused_tuning;
+
+/* Workspace bytes of numarck_compress_batch_fused for this item list: 256 bytes of control,
+ * the variables' descriptors and work-list tables, and one numarck_workspace_bytes slice per
+ * variable (about 41 MiB each). 0 if an item is invalid (B = 0 is rejected: the automatic
+ * index length synchronises). */
+size_t numarck_fused_workspace_bytes(const numarck_batch_item* items, int count);
+
+/* Compresses count variables with the fused launches. ws: device workspace of
+ * >= numarck_fused_workspace_bytes bytes, 256-byte aligned, zero-filled before first use
+ * (numarck_workspace_init). A call leaves it ready for the next call with the same item list
+ * (the same n and params per position); a workspace that served a different list must be
+ * zero-filled again, because each variable's slice sits at an offset that depends on the
+ * sizes before it. Every item is validated on the host before any launch; the return value is
+ * the first error found (nothing is queued then), else NUMARCK_OK once the work is queued on
+ * `stream`. Device-side errors go to each blob's status word as for numarck_compress. The call
+ * is a fixed sequence of launches on `stream` (no host synchronisation), so it can be captured
+ * into a CUDA graph and replayed with new data in the same buffers. */
+int numarck_compress_batch_fused(const numarck_batch_item* items, int count,
+                                 const numarck_fused_tuning* tuning, void* ws, size_t ws_bytes,
+                                 numarck_stream_t stream);
+
+/* Workspace bytes of numarck_decompress_batch_fused: the blobs' descriptors and tile table. */
+size_t numarck_fused_decode_workspace_bytes(int count);
+
+/* Decompresses count blobs (Eq. 4) with one prep launch (the blob headers validated on the
+ * device, the tile table built) and one decode launch over all blobs' tiles. ws: device buffer
+ * of >= numarck_fused_decode_workspace_bytes(count) bytes, 256-byte aligned (no
+ * initialisation needed). status_dev as in numarck_decompress (shared by all items; may be
+ * NULL): a blob whose header is invalid or whose n differs from the item's is not decoded and
+ * reports its error there. Capturable into a CUDA graph like the compression. */
+int numarck_decompress_batch_fused(const numarck_batch_decode_item* items, int count,
+                                   const numarck_fused_tuning* tuning, void* ws, size_t ws_bytes,
+                                   int32_t* status_dev, numarck_stream_t stream);
+
 /* ---- tracing (kernel-level timing for profilers and benchmarks) ----
  * events : an array of `count` cudaEvent_t handles owned by the caller, or NULL to stop.
  * While set, every numarck_compress call made on this host thread records, on its stream,
@@ -364,7 +428,9 @@ int numarck_decompress_batch(const numarck_batch_decode_item* items, int count, 
  * kernel(s), the top-k kernel, the assign + pack kernel, the offset-table scan and the
  * incompressible-value copy; every numarck_decompress[_range] call records events[0] before and
  * events[1] after its kernel. A call needs count >= 6 (compress) or >= 2 (decompress) to record
- * anything.
+ * anything. A numarck_compress_batch_fused call records events[0] before its first launch and
+ * events[1..5] after its ratio/histogram, top-k, indexing, offset-scan and incompressible-copy
+ * launches; a numarck_decompress_batch_fused call events[0] and events[1] around its launches.
  * Returns NUMARCK_ERR_INVALID_ARG if count < 0. */
 int numarck_trace_events(void* const* events, int count);
 

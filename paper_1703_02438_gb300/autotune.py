@@ -1,5 +1,14 @@
-"""Autotuner for batched compression: picks the number of concurrent lanes and the grid share
-(each variable's kernels sized for 1/grid_share of the GPU) by timing the actual batch.
+"""Autotuner for batched compression: times the actual batch (compression and decompression)
+under every candidate configuration and keeps the fastest.
+
+Two families of configurations give byte-identical results:
+  * lanes (numarck_compress_batch): `lanes` variables in flight on forked streams, each
+    variable's kernels sized for 1/grid_share of the GPU;
+  * fused (numarck_compress_batch_fused): one launch per phase over a work list of variables;
+    the shape knobs are the CTA size of the ratio/histogram pass (512 or 1024 threads), the
+    warps per CTA of the incompressible copy (4 or 8), how many warps share a 4096-element tile
+    in the decode (2^decode_seg_log2), and how many work lists (groups) run on how many streams
+    (each launch sized for 1/streams of the GPU).
 
 The best setting is cached per (GPU name, batch signature) in _lib/autotune.json next to the
 built library, so later runs of a batch with the same shape reuse it without timing again.
@@ -14,7 +23,9 @@ import torch
 
 from . import numarck as N
 
-CANDIDATES = ((1, 1), (2, 2), (4, 2), (4, 4), (8, 4), (8, 8), (16, 8), (16, 16), (32, 16))
+LANE_CANDIDATES = ((1, 1), (2, 2), (4, 2), (4, 4), (8, 4), (8, 8), (16, 8), (16, 16), (32, 16))
+FUSED_CANDIDATES = tuple((k1, xw, sl, g, st) for k1 in (512, 1024) for xw, sl in ((8, 0), (4, 1))
+                         for g, st in ((1, 1), (4, 2), (8, 2), (8, 4), (16, 4)))
 _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "autotune.json")
 
 
@@ -33,39 +44,59 @@ def _load():
         return {}
 
 
-def _time(batch: N.Batch, reps: int) -> float:
-    batch.run()
+def _time(batch: N.Batch, prevs, outs, reps: int) -> float:
+    """Mean ms of one compression of the batch plus one decompression of its blobs."""
+    def once():
+        batch.run()
+        batch.decompress(prevs, outs=outs)
+    once()
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
     for _ in range(reps):
-        batch.run()
+        once()
     b.record()
     torch.cuda.synchronize()
     return a.elapsed_time(b) / reps
 
 
-def tune(batch: N.Batch, reps: int = 2, candidates=CANDIDATES, use_cache: bool = True):
-    """Sets batch.lanes / batch.grid_share to the fastest candidate; returns
-    (lanes, grid_share, {candidate: ms})."""
+def _apply(batch: N.Batch, key: str):
+    kind, rest = key.split(":")
+    vals = [int(v) for v in rest.split("x")]
+    if kind == "lanes":
+        batch.set_lanes(*vals)
+    else:
+        batch.set_fused(tuple(vals))
+
+
+def tune(batch: N.Batch, reps: int = 2, lane_candidates=LANE_CANDIDATES,
+         fused_candidates=FUSED_CANDIDATES, use_cache: bool = True):
+    """Sets the batch to the fastest candidate; returns (best key, {key: ms}). Keys are
+    "lanes:<lanes>x<grid_share>" and
+    "fused:<k1_threads>x<exact_warps>x<decode_seg_log2>x<groups>x<streams>"."""
     key = torch.cuda.get_device_name() + "|" + signature(batch)
     cache = _load() if use_cache else {}
     if key in cache:
-        lanes, share = cache[key]["best"]
-        batch.set_lanes(lanes, share)
-        return lanes, share, cache[key]["ms"]
+        _apply(batch, cache[key]["best"])
+        return cache[key]["best"], cache[key]["ms"]
+    prevs = [p for p, _ in batch.pairs]
+    outs = [torch.empty_like(p) for p in prevs]
     timings = {}
-    for lanes, share in candidates:
-        batch.set_lanes(lanes, share)
-        timings[f"{lanes}x{share}"] = _time(batch, reps)
+    for lanes, share in lane_candidates:
+        k = f"lanes:{lanes}x{share}"
+        _apply(batch, k)
+        timings[k] = _time(batch, prevs, outs, reps)
+    for cand in fused_candidates:
+        k = "fused:" + "x".join(str(v) for v in cand)
+        _apply(batch, k)
+        timings[k] = _time(batch, prevs, outs, reps)
     best = min(timings, key=timings.get)
-    lanes, share = (int(v) for v in best.split("x"))
-    batch.set_lanes(lanes, share)
-    cache[key] = {"best": [lanes, share], "ms": timings}
+    _apply(batch, best)
+    cache[key] = {"best": best, "ms": timings}
     try:
         os.makedirs(os.path.dirname(_CACHE), exist_ok=True)
         with open(_CACHE, "w") as f:
             json.dump(cache, f, indent=1)
     except OSError:
         pass
-    return lanes, share, timings
+    return best, timings

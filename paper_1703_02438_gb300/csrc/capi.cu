@@ -119,10 +119,7 @@ bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 thread_local void* const* g_trace = nullptr;
 thread_local int g_trace_count = 0;
 
-void trace(int i, int need, cudaStream_t s) {
-  if (g_trace && g_trace_count >= need && g_trace[i])
-    cudaEventRecord(static_cast<cudaEvent_t>(g_trace[i]), s);
-}
+void trace(int i, int need, cudaStream_t s) { trace_event(i, need, s); }
 
 int decode(const void* blob, const void* header_host, const void* prev_seg, int64_t start,
            int64_t count, void* out_seg, int64_t n_expected, int32_t* status_dev,
@@ -194,6 +191,11 @@ int numarck_workspace_init(void* ws, size_t ws_bytes, numarck_stream_t stream) {
 
 namespace nmk {
 
+void trace_event(int i, int need, cudaStream_t s) {
+  if (g_trace && g_trace_count >= need && g_trace[i])
+    cudaEventRecord(static_cast<cudaEvent_t>(g_trace[i]), s);
+}
+
 // Validates the arguments of one compression and fills its launch plan (no device access).
 int plan_compress(const void* prev, const void* cur, int64_t n, const numarck_params* p,
                   void* blob, size_t blob_cap, void* ws, size_t ws_bytes, CompressPlan* out) {
@@ -228,29 +230,7 @@ int plan_compress(const void* prev, const void* cur, int64_t n, const numarck_pa
   else
     P.cf = make_consts<float>(p->E, p->anchor);
 
-  numarck_header& h = P.hdr;
-  std::memset(&h, 0, sizeof(h));
-  h.magic = NUMARCK_MAGIC;
-  h.version = NUMARCK_VERSION;
-  h.dtype = p->dtype;
-  h.B = p->B ? p->B : NUMARCK_MAX_B;
-  h.E = p->E;
-  h.anchor = p->anchor;
-  h.status = 0;
-  h.n = n;
-  h.block_bytes = bb;
-  h.epb = g.epb;
-  h.nblocks = g.nblocks;
-  h.sub = SUB;
-  h.nsub = g.nsub;
-  h.block_stride = g.block_stride;
-  h.off_centres = g.off_centres;
-  h.off_idx_off = g.off_idx_off;
-  h.off_inc_off = g.off_inc_off;
-  h.off_sub_off = g.off_sub_off;
-  h.off_index = g.off_index;
-  h.off_exact = g.off_exact;
-  h.total_bytes = g.off_exact;
+  P.hdr = make_header(g, p->E, bb);
   return NUMARCK_OK;
 }
 

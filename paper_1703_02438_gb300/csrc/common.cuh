@@ -25,6 +25,7 @@ constexpr int HMARGIN = 8;                      // spare bins at each end of the
 constexpr int SH_BINS = 16384;                  // K1 shared-memory histogram window
 constexpr int DM_SMEM = 4096;                   // K4 multipliers kept in shared memory
 constexpr unsigned KEY_BIAS = 0x40000000u;      // bin-range keys: 0 means "no value"
+constexpr int SCAN_TILE = 4096;                 // per-tile counts one offset-scan CTA covers
 // Per-element codes written by K1 and read by K3. For a binnable point whose bin b lies in the
 // code window [code_base, code_base + CODE_BINS) (code_base = zero-change bin - 16383):
 // code = (b - code_base) << 1 | pass, where pass is the error-bound check of §III.C against the
@@ -119,6 +120,36 @@ __host__ __device__ __forceinline__ int64_t code_offset(const Geometry& g) {
   return (g.off_exact + g.n * ((g.dtype == NUMARCK_F64 ? 8 : 4) - 2)) & ~(int64_t)15;
 }
 
+// The header of a compression as known before its kernels run (status, n_sel, n_inc and a are
+// 0; the kernels fill them in): magic, version, parameters and the section offsets of g.
+__host__ __device__ inline numarck_header make_header(const Geometry& g, double E,
+                                                      int64_t block_bytes) {
+  numarck_header h;
+  unsigned char* raw = reinterpret_cast<unsigned char*>(&h);
+  for (int i = 0; i < (int)sizeof(h); ++i) raw[i] = 0;
+  h.magic = NUMARCK_MAGIC;
+  h.version = NUMARCK_VERSION;
+  h.dtype = g.dtype;
+  h.B = g.B;
+  h.E = E;
+  h.anchor = g.anchor;
+  h.n = g.n;
+  h.block_bytes = block_bytes;
+  h.epb = g.epb;
+  h.nblocks = g.nblocks;
+  h.sub = SUB;
+  h.nsub = g.nsub;
+  h.block_stride = g.block_stride;
+  h.off_centres = g.off_centres;
+  h.off_idx_off = g.off_idx_off;
+  h.off_inc_off = g.off_inc_off;
+  h.off_sub_off = g.off_sub_off;
+  h.off_index = g.off_index;
+  h.off_exact = g.off_exact;
+  h.total_bytes = g.off_exact;
+  return h;
+}
+
 // Checks a header against the geometry its own fields imply. Returns 0 or NUMARCK_ERR_CORRUPT
 // (or the header's non-zero device status).
 __host__ __device__ inline int check_header(const numarck_header& h, Geometry* out) {
@@ -192,6 +223,30 @@ __device__ __forceinline__ bool bounded_wait(const unsigned long long* p,
       if ((spins & 63u) == 0 && global_timer_ns() - t0 > limit_ns) return false;
     }
   }
+}
+
+// 16-byte asynchronous copies global -> shared (cp.async, bypassing L1), committed as a group.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n"
+               :: "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Index v of the variable whose range [pre[v], pre[v+1]) holds x, for a non-decreasing prefix
+// table pre[0..count] with pre[0] = 0 <= x < pre[count] (variables with empty ranges are
+// skipped: the largest v with pre[v] <= x).
+__device__ __forceinline__ int find_var(const long long* pre, int count, long long x) {
+  int lo = 0, hi = count;          // pre[lo] <= x < pre[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pre[mid] <= x) lo = mid; else hi = mid;
+  }
+  return lo;
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {

@@ -161,4 +161,189 @@ __device__ __forceinline__ void k1_end(const HistCtx& h, int lmin, int lmax) {
   }
 }
 
+
+// ---------------------------------------------------------------------------------------
+// The loops of K0 and K1 over a range of one variable, shared by the single-variable kernels
+// (k_hist.cu: the whole variable, a grid-stride loop) and the fused batch kernels (k_fused.cu:
+// a CTA's contiguous part of each variable it covers).
+// ---------------------------------------------------------------------------------------
+constexpr int K1_UNROLL = 2;                        // 16-byte vectors of each input per lane per step
+constexpr int K1_STAGE = 2 * K1_UNROLL * 32 * 16;   // bytes of a warp's stage (prev, cur)
+
+// Grid origin of the MIN grid from the minimum-ratio key K0 left in the control block.
+template <typename T>
+__device__ __forceinline__ void anchor_min_consts(Consts<T>& c, const Ctrl* ctrl) {
+  const unsigned long long key = ctrl->amin_key;
+  double a = key ? key_to_ratio(key) : 0.0;
+  if (a == 0.0) a = 0.0;  // a zero minimum is taken as +0
+  c.a = (T)a;             // exact: the key was made from a T value
+  c.af = (float)c.a;
+  c.K0 = __fadd_ru(__fmul_ru(__fmul_ru(0x1p-18f, c.inv_wf), fabsf(c.af)), 0x1p-60f);
+  c.C0 = __fmaf_ru(0x1p-22f, fabsf(c.af), __fadd_ru(0x1.8p-49f, 0x1p-100f));
+}
+
+// Bin of a zero change ratio (the centre of K1's shared window and of its code window).
+template <typename T>
+__device__ __forceinline__ int zero_change_bin(const Consts<T>& c, bool anchor_min) {
+  if (!anchor_min) return 0;
+  const double z = floor(-(double)c.a * (double)c.inv_w);
+  return (int)fmin(fmax(z, 0.0), (double)(1 << (WIN_LOG2 + 1)));
+}
+
+// K0's per-thread part: the largest order key (= smallest binnable ratio) over elements
+// j0, j0 + stride, ... < j1. Returns 0 if none is binnable.
+template <typename T>
+__device__ __forceinline__ unsigned long long k0_range(const T* __restrict__ prev,
+                                                       const T* __restrict__ cur, int64_t j0,
+                                                       int64_t j1, int64_t stride,
+                                                       const Consts<T>& c) {
+  unsigned long long best = 0;
+  for (int64_t j = j0; j < j1; j += stride) {
+    const T p = ld_stream(prev + j), x = ld_stream(cur + j);
+    const T d = t_sub(x, p);
+    const T r = t_div(d, p);
+    if (t_abs(r) <= c.cap) {
+      const unsigned long long k = min_key(r);
+      best = k > best ? k : best;
+    }
+  }
+  return best;
+}
+
+// One warp's K0 result into the control block's key (lane 0, one atomic).
+__device__ __forceinline__ void k0_publish(unsigned long long best, Ctrl* ctrl) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, best, o);
+    best = t > best ? t : best;
+  }
+  if (lane_id() == 0 && best) atomicMax(&ctrl->amin_key, best);
+}
+
+// K1 over 16-byte vectors [v_lo, v_hi) of one variable (prev and cur 16-byte aligned): warp wid
+// of nw takes the steps starting at v_lo + wid * 32 U, then every nw * 32 U vectors, each step
+// 32 U vectors of both inputs (U = K1_UNROLL, lane l holds vectors u * 32 + l). Each warp copies
+// its next step into its stage (cp.async, K1_STAGE bytes of shared memory at `stage`) before it
+// classifies the current one. Codes go to codes[element], bins to the histograms of h.
+template <typename T>
+__device__ __forceinline__ void k1_vec_range(const HistCtx& h, const Consts<T>& c,
+                                             const T* __restrict__ prev,
+                                             const T* __restrict__ cur, int64_t v_lo,
+                                             int64_t v_hi, int64_t wid, int64_t nw,
+                                             unsigned char* stage, int& lmin, int& lmax) {
+  using V = Vec<T>;
+  using VT = typename V::type;
+  const int lane = (int)lane_id();
+  const VT* pv = reinterpret_cast<const VT*>(prev);
+  const VT* xv = reinterpret_cast<const VT*>(cur);
+  unsigned short* codes = h.codes;
+  // this lane's slots of the warp's stage: [u][lane] prev vectors, then cur vectors; a lane
+  // reads back only what it copied itself
+  VT* sp = reinterpret_cast<VT*>(stage);
+  VT* sx = sp + K1_UNROLL * 32;
+  const int64_t step = nw * (32 * K1_UNROLL);
+  auto stage_step = [&](int64_t b0) {
+#pragma unroll
+    for (int u = 0; u < K1_UNROLL; ++u) {
+      const int64_t vi = b0 + u * 32 + lane;
+      if (vi < v_hi) {
+        cp_async16(sp + u * 32 + lane, pv + vi);
+        cp_async16(sx + u * 32 + lane, xv + vi);
+      }
+    }
+    cp_async_commit();
+  };
+  const int64_t first = v_lo + wid * (32 * K1_UNROLL);
+  if (first < v_hi) stage_step(first);
+  for (int64_t base = first; base < v_hi; base += step) {
+    T pe[K1_UNROLL][V::N], xe[K1_UNROLL][V::N];
+    bool ok[K1_UNROLL];
+    cp_async_wait_all();
+#pragma unroll
+    for (int u = 0; u < K1_UNROLL; ++u) {
+      const int64_t vi = base + u * 32 + lane;
+      ok[u] = vi < v_hi;
+      VT a = {}, b = {};
+      if (ok[u]) { a = sp[u * 32 + lane]; b = sx[u * 32 + lane]; }
+      V::get(a, pe[u]);
+      V::get(b, xe[u]);
+    }
+    if (base + step < v_hi) stage_step(base + step);   // in flight while this step is classified
+    unsigned pend = 0;   // bit u * V::N + v: element needs the exact sequences
+#pragma unroll
+    for (int u = 0; u < K1_UNROLL; ++u) {
+      const int64_t vi = base + u * 32 + lane;
+      unsigned cw[V::N];
+#pragma unroll
+      for (int v = 0; v < V::N; ++v) {
+        int b = 0;
+        bool pass = false;
+        const int kind = ok[u] ? Classifier<T>::fast(pe[u][v], xe[u][v], c, h.cbase, b, pass) : 0;
+        const bool binned = kind == 1;
+        if (kind >= 2) pend |= 1u << (u * V::N + v);
+        cw[v] = bin_code(h, binned, b, pass);
+        hist_add(h, binned, b, lmin, lmax);
+      }
+      if (ok[u]) reinterpret_cast<typename V::codes*>(codes)[vi] = V::pack(cw);
+    }
+    // settle undecided elements (rare) with the exact sequences, one per lane per round
+    while (__any_sync(0xffffffffu, pend != 0u)) {
+      int b = 0;
+      bool binned = false, pass = false;
+      if (pend) {
+        const int k = __ffs(pend) - 1;
+        pend &= pend - 1;
+        const int u = k / V::N, v = k % V::N;
+        const int64_t j = (base + u * 32 + lane) * V::N + v;   // reloaded: keeps pe, xe short-lived
+        binned = Classifier<T>::exact(prev[j], cur[j], c, h.cbase, b, pass) == 1;
+        codes[j] = (unsigned short)bin_code(h, binned, b, pass);
+      }
+      hist_add(h, binned, b, lmin, lmax);
+    }
+  }
+}
+
+// K1 over elements [j_lo, j_hi) with scalar loads (any alignment; also the tail after the last
+// whole vector): warp wid of nw takes steps of 32 U elements from j_lo + wid * 32 U.
+template <typename T, int U>
+__device__ __forceinline__ void k1_scalar_range(const HistCtx& h, const Consts<T>& c,
+                                                const T* __restrict__ prev,
+                                                const T* __restrict__ cur, int64_t j_lo,
+                                                int64_t j_hi, int64_t wid, int64_t nw, int& lmin,
+                                                int& lmax) {
+  const int lane = (int)lane_id();
+  for (int64_t base = j_lo + wid * (32 * U); base < j_hi; base += nw * (32 * U)) {
+    T pe[U], xe[U];
+    bool ok[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t j = base + u * 32 + lane;
+      ok[u] = j < j_hi;
+      pe[u] = ok[u] ? ld_stream(prev + j) : (T)0;
+      xe[u] = ok[u] ? ld_stream(cur + j) : (T)0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      int b = 0;
+      bool pass = false;
+      const bool binned = ok[u] && Classifier<T>::exact(pe[u], xe[u], c, h.cbase, b, pass) == 1;
+      if (ok[u]) h.codes[base + u * 32 + lane] = (unsigned short)bin_code(h, binned, b, pass);
+      hist_add(h, binned, b, lmin, lmax);
+    }
+  }
+}
+
+// Clears the per-tile counts of the tiles holding elements [e0, e1) of a variable (a K1 pass
+// leaves them zero for K3a), all threads of the CTA; with `scan_flags` also the offset scan's
+// look-back flags after them.
+__device__ __forceinline__ void clear_tile_counts(unsigned long long* tstatus, const Geometry& g,
+                                                  int64_t e0, int64_t e1, bool scan_flags) {
+  if (e1 <= e0) return;
+  const int64_t q0 = e0 / g.epb, q1 = (e1 - 1) / g.epb;
+  const int64_t t0 = q0 * g.spb + (e0 - q0 * g.epb) / SUB;
+  int64_t t1 = q1 * g.spb + (e1 - 1 - q1 * g.epb) / SUB + 1;
+  if (scan_flags) t1 = g.nsub + g.nsub / 4096 + 2;
+  for (int64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x) tstatus[i] = 0ull;
+}
+
 }  // namespace nmk

@@ -245,13 +245,14 @@ __device__ __forceinline__ void shifted_codes(const unsigned (&win)[NW + 4], int
 // their codes one by one.
 template <int B, typename T>
 __device__ __forceinline__ void k3a_tiles(const AssignArgs<T>& A, const unsigned short* s_tab,
-                                          long long W, int lane, int tid, int any) {
+                                          long long gt_begin, long long gt_end, long long W,
+                                          int lane, int any) {
   constexpr unsigned M = (1u << B) - 1u;
   constexpr bool kSentinel = B < 16;             // see k3_assign
   constexpr int EL = B % 2 == 0 ? 16 : 32, NW = EL / 2, NV = EL / 8, WL = EL * B / 32;
   constexpr int SEGW = 32 * EL;
   const Geometry& g = A.g;
-  for (long long gt = (long long)blockIdx.x * K3_WARPS + (tid >> 5); gt < g.nsub; gt += W) {
+  for (long long gt = gt_begin; gt < gt_end; gt += W) {
     const TileRef tr = tile_ref<B>(g, gt, A.blob, A.codes);
     const int cnt = tr.cnt;
     const int sh = (int)(tr.j0 & 7);
@@ -345,40 +346,65 @@ __device__ __forceinline__ void k3a_tiles(const AssignArgs<T>& A, const unsigned
   }
 }
 
+// K3a's table of the index of every 16-bit code, built by all threads of the CTA (ends with a
+// block barrier; the table is read-only afterwards): every code is a marker (M) except the pass
+// codes of selected bins, which take the bin's rank. CODE_FAR's entry: a value above M when
+// B < 16 (max() over a tile finds far points, min() turns them into markers); M when B = 16,
+// where far points are found by comparing codes.
 template <typename T, int B>
-__global__ void __launch_bounds__(K3_THREADS, 1) k3_assign(AssignArgs<T> A) {
+__device__ __forceinline__ void k3a_table(const AssignArgs<T>& A, unsigned short* s_tab, int any) {
   constexpr unsigned M = (1u << B) - 1u;
-  // CODE_FAR's entry: a value above M when B < 16 (max() over a tile finds far points, min()
-  // turns them into markers); M when B = 16, where far points are found by comparing codes
-  constexpr bool kSentinel = B < 16;
-  constexpr unsigned FARV = kSentinel ? 0xFFFFu : M;
-  extern __shared__ __align__(16) unsigned short s_tab[];   // [65536]: index of each code
-
+  constexpr unsigned FARV = B < 16 ? 0xFFFFu : M;
   const Ctrl* ctrl = A.ctrl;
   const int tid = (int)threadIdx.x;
-  const int lane = (int)lane_id();
-  const int any = ctrl->any;
   const int cbase = ctrl->code_base;
   const int slo = any ? ctrl->sel_lo : 1, shi = any ? ctrl->sel_hi : 0;
-
-  // every code is a marker (M) except the pass codes of selected bins, which take the bin's rank
   const uint4 fill = make_uint4(M | (M << 16), M | (M << 16), M | (M << 16), M | (M << 16));
-  for (int i = tid; i < 65536 / 8; i += K3_THREADS) reinterpret_cast<uint4*>(s_tab)[i] = fill;
+  for (int i = tid; i < 65536 / 8; i += blockDim.x) reinterpret_cast<uint4*>(s_tab)[i] = fill;
   __syncthreads();
   const int blo = max(slo, cbase), bhi = min(shi, cbase + CODE_BINS - 1);
-  for (int b = blo + tid; b <= bhi; b += K3_THREADS)
+  for (int b = blo + tid; b <= bhi; b += blockDim.x)
     s_tab[((b - cbase) << 1) | 1] = A.rank_of[b - A.c.hbase];
   if (tid == 0) s_tab[CODE_FAR] = (unsigned short)FARV;
-  __syncthreads();   // the only block-wide barriers: the table is read-only from here on
+  __syncthreads();
+}
 
+template <typename T, int B>
+__global__ void __launch_bounds__(K3_THREADS, 1) k3_assign(AssignArgs<T> A) {
+  extern __shared__ __align__(16) unsigned short s_tab[];   // [65536]: index of each code
+  const int any = A.ctrl->any;
+  k3a_table<T, B>(A, s_tab, any);   // the only block-wide barriers
   const long long W = (long long)gridDim.x * K3_WARPS;
-  k3a_tiles<B>(A, s_tab, W, lane, tid, any);
+  k3a_tiles<B>(A, s_tab, (long long)blockIdx.x * K3_WARPS + (threadIdx.x >> 5), A.g.nsub, W,
+               (int)lane_id(), any);
 }
 
 // K3f — tiles with points outside K1's code window (flagged by K3a; rare: a bin more than 16383
 // bins from the zero-change bin). Each such tile is indexed again from prev and cur with the
 // exact sequences (bin, rank, check of §III.C against the selected centre), replacing K3a's
 // image, ballots and count. The tile's codes are not used (K3a has written ballots over them).
+// K3f's work on one flagged tile gt (one warp).
+template <typename T, int B>
+__device__ __forceinline__ void k3f_tile(const AssignArgs<T>& A, const Consts<T>& c,
+                                         const RankView& rv, long long gt, int lane) {
+  constexpr unsigned M = (1u << B) - 1u;
+  const TileRef tr = tile_ref<B>(A.g, gt, A.blob, A.codes);
+  int count = 0;
+  for (int sb0 = 0; sb0 < tr.cnt; sb0 += K3_SEG) {
+    unsigned idx[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int e = sb0 + lane * 4 + k;
+      const long long j = tr.j0 + e;
+      idx[k] = e < tr.cnt ? FarAssigner<T>::index(A.prev[j], A.cur[j], c, rv, A.mtab, A.cftab, M)
+                          : M;
+    }
+    step_out<B>(idx, sb0, tr.cnt, lane, tr.halves, tr.tw, tr.twords, count);
+  }
+  count = __reduce_add_sync(0xffffffffu, count);
+  if (lane == 0) A.tstatus[gt] = (unsigned long long)count;
+}
+
 template <typename T, int B>
 __global__ void __launch_bounds__(K3_THREADS) k3_fixup(AssignArgs<T> A) {
   constexpr unsigned M = (1u << B) - 1u;
@@ -392,21 +418,7 @@ __global__ void __launch_bounds__(K3_THREADS) k3_fixup(AssignArgs<T> A) {
   for (long long gt = (long long)blockIdx.x * K3_WARPS + (threadIdx.x >> 5); gt < g.nsub;
        gt += W) {
     if (!(A.tstatus[gt] & K3_FAR_FLAG)) continue;   // uniform across the warp
-    const TileRef tr = tile_ref<B>(g, gt, A.blob, A.codes);
-    int count = 0;
-    for (int sb0 = 0; sb0 < tr.cnt; sb0 += K3_SEG) {
-      unsigned idx[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int e = sb0 + lane * 4 + k;
-        const long long j = tr.j0 + e;
-        idx[k] = e < tr.cnt ? FarAssigner<T>::index(A.prev[j], A.cur[j], c, rv, A.mtab, A.cftab, M)
-                            : M;
-      }
-      step_out<B>(idx, sb0, tr.cnt, lane, tr.halves, tr.tw, tr.twords, count);
-    }
-    count = __reduce_add_sync(0xffffffffu, count);
-    if (lane == 0) A.tstatus[gt] = (unsigned long long)count;
+    k3f_tile<T, B>(A, c, rv, gt, lane);
   }
 }
 
@@ -419,19 +431,18 @@ __global__ void __launch_bounds__(K3_THREADS) k3_fixup(AssignArgs<T> A) {
 constexpr int SC_THREADS = 1024;
 constexpr int SC_PER = 4;
 constexpr int SC_TILE = SC_THREADS * SC_PER;
+static_assert(SC_TILE == SCAN_TILE, "the host plans scan blocks of SCAN_TILE counts");
 constexpr unsigned long long SC_AGG = 1ull << 62, SC_INC = 2ull << 62, SC_VAL = (1ull << 62) - 1;
 constexpr unsigned long long SC_LIMIT_NS = 2000000000ull;
 
-__global__ void __launch_bounds__(SC_THREADS, 1) k3_scan(const unsigned long long* counts,
-                                                        unsigned long long* flags, Ctrl* ctrl,
-                                                        Geometry g, unsigned char* blob, int L) {
+// Block blk of the scan of one variable (all threads of the CTA; blocks of a variable must be
+// started in increasing order, each only after the ones before it have been started).
+__device__ __forceinline__ void k3_scan_block(const unsigned long long* counts,
+                                              unsigned long long* flags, long long blk,
+                                              const Geometry& g, unsigned char* blob, int L) {
   __shared__ long long s_w[33];
   __shared__ long long s_P;
-  __shared__ long long s_blk;
   const int tid = (int)threadIdx.x;
-  if (tid == 0) s_blk = (long long)atomicAdd(&ctrl->ticket, 1u);
-  __syncthreads();
-  const long long blk = s_blk;
   const long long lo = blk * SC_TILE + (long long)tid * SC_PER;
   long long v[SC_PER];
   long long sum = 0;
@@ -508,6 +519,15 @@ __global__ void __launch_bounds__(SC_THREADS, 1) k3_scan(const unsigned long lon
   }
 }
 
+__global__ void __launch_bounds__(SC_THREADS, 1) k3_scan(const unsigned long long* counts,
+                                                        unsigned long long* flags, Ctrl* ctrl,
+                                                        Geometry g, unsigned char* blob, int L) {
+  __shared__ long long s_blk;
+  if (threadIdx.x == 0) s_blk = (long long)atomicAdd(&ctrl->ticket, 1u);
+  __syncthreads();
+  k3_scan_block(counts, flags, s_blk, g, blob, L);
+}
+
 // K3c — incompressible values (§III.C). Each warp takes a tile: it gets the tile's marker flags
 // as 32-bit ballots (one per 32-element step), compacts the positions of the set bits into a
 // per-warp list in shared memory (popcounts and a warp scan give each step its place), then
@@ -524,25 +544,18 @@ constexpr int K3X_THREADS = K3X_WARPS * 32;
 constexpr int K3X_UNROLL = 4;
 constexpr int K3X_SMEM = K3X_WARPS * SUB * 2;   // per warp: up to SUB u16 positions
 
+// K3c's work on tile gt of one variable (one warp; `list` is the warp's SUB u16 of shared memory).
 template <typename T>
-__global__ void __launch_bounds__(K3X_THREADS) k3_exact(const T* __restrict__ cur,
-                                                        const unsigned short* codes, Geometry g,
-                                                        unsigned char* blob, long long code_off) {
-  extern __shared__ __align__(16) unsigned short k3x_list[];
+__device__ __forceinline__ void k3x_tile(const T* __restrict__ cur, const unsigned short* codes,
+                                         const Geometry& g, unsigned char* blob, bool from_codes,
+                                         long long gt, unsigned short* list, int lane) {
   using U = typename Bits<T>::U;
-  const int lane = (int)lane_id();
-  unsigned short* list = k3x_list + (threadIdx.x >> 5) * SUB;
-  const long long W = (long long)gridDim.x * K3X_WARPS;
   U* exact_u = reinterpret_cast<U*>(blob + g.off_exact);
   const int64_t* sub_off = reinterpret_cast<const int64_t*>(blob + g.off_sub_off);
   const U* xu = reinterpret_cast<const U*>(cur);
-  const long long L = (long long)sizeof(T);
-  const long long n_inc = reinterpret_cast<const numarck_header*>(blob)->n_inc;
-  const bool from_codes = g.off_exact + n_inc * L <= code_off;
   const int B = g.B;
   const unsigned M = (unsigned)g.M, fmask = (1u << B) - 1u;
-  for (long long gt = (long long)blockIdx.x * K3X_WARPS + (threadIdx.x >> 5); gt < g.nsub;
-       gt += W) {
+  {
     const long long q = gt / g.spb, t = gt - q * g.spb;
     const long long j0 = q * g.epb + t * SUB;
     const long long bend = min((long long)g.n, (long long)((q + 1) * g.epb));
@@ -616,6 +629,174 @@ __global__ void __launch_bounds__(K3X_THREADS) k3_exact(const T* __restrict__ cu
     }
     __syncwarp();   // the list is rebuilt for the next tile
   }
+}
+
+// Whether K3c takes a variable's marker flags from the half-ballots K3a left in its code area
+// (see above), decided from the variable's n_inc.
+template <typename T>
+__device__ __forceinline__ bool k3x_from_codes(const Geometry& g, const unsigned char* blob,
+                                               long long code_off) {
+  const long long n_inc = reinterpret_cast<const numarck_header*>(blob)->n_inc;
+  return g.off_exact + n_inc * (long long)sizeof(T) <= code_off;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(K3X_THREADS) k3_exact(const T* __restrict__ cur,
+                                                        const unsigned short* codes, Geometry g,
+                                                        unsigned char* blob, long long code_off) {
+  extern __shared__ __align__(16) unsigned short k3x_list[];
+  const int lane = (int)lane_id();
+  unsigned short* list = k3x_list + (threadIdx.x >> 5) * SUB;
+  const long long W = (long long)gridDim.x * K3X_WARPS;
+  const bool from_codes = k3x_from_codes<T>(g, blob, code_off);
+  for (long long gt = (long long)blockIdx.x * K3X_WARPS + (threadIdx.x >> 5); gt < g.nsub;
+       gt += W)
+    k3x_tile<T>(cur, codes, g, blob, from_codes, gt, list, lane);
+}
+
+// ---------------------------------------------------------------------------------------
+// Fused batch (K6): K3a + K3f, K3b and K3c of every variable of a batch, one launch each.
+// The work list of K3a/K3f and K3c is the concatenation of the variables' tiles (tpre), that of
+// K3b the concatenation of their scan blocks (spre).
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ Consts<T> fused_consts(const FusedVar& V);
+template <>
+__device__ __forceinline__ Consts<double> fused_consts<double>(const FusedVar& V) { return V.cd; }
+template <>
+__device__ __forceinline__ Consts<float> fused_consts<float>(const FusedVar& V) { return V.cf; }
+
+template <typename T>
+__device__ __forceinline__ AssignArgs<T> fused_assign_args(const FusedVar& V) {
+  AssignArgs<T> A;
+  A.prev = static_cast<const T*>(V.prev);
+  A.cur = static_cast<const T*>(V.cur);
+  A.c = fused_consts<T>(V);
+  A.g = V.g;
+  A.ctrl = reinterpret_cast<Ctrl*>(V.ws + V.wl.ctrl);
+  A.rank_of = reinterpret_cast<const unsigned short*>(V.ws + V.wl.rank);
+  A.mtab = reinterpret_cast<const T*>(V.ws + V.wl.mtab);
+  A.cftab = reinterpret_cast<const float*>(V.ws + V.wl.cftab);
+  A.tstatus = reinterpret_cast<unsigned long long*>(V.ws + V.wl.status);
+  A.blob = V.blob;
+  A.codes = reinterpret_cast<const unsigned short*>(V.blob + V.code_off);
+  return A;
+}
+
+// K3a over tiles [t0, t1) of one variable by all warps of the CTA (the code table built for this
+// variable first), then K3f by each warp on the tiles it flagged. A is the variable's argument
+// block in shared memory (read in place: a copy in registers would not fit beside the loop).
+template <typename T, int B>
+__device__ __forceinline__ void k3_fused_part(const AssignArgs<T>& A, long long t0, long long t1,
+                                              unsigned short* s_tab) {
+  constexpr unsigned M = (1u << B) - 1u;
+  const int any = A.ctrl->any;
+  const int lane = (int)lane_id(), warp = (int)(threadIdx.x >> 5);
+  k3a_table<T, B>(A, s_tab, any);
+  k3a_tiles<B>(A, s_tab, t0 + warp, t1, K3_WARPS, lane, any);
+  __syncwarp();      // the tile counts (and flags) lane 0 stored are visible to the warp
+  if (!any) return;
+  Consts<T> c = A.c;
+  anchor_consts<T>(c, A.g, A.ctrl);
+  const RankView rv{A.rank_of, c.hbase, A.ctrl->sel_lo, A.ctrl->sel_hi, M};
+  for (long long gt = t0 + warp; gt < t1; gt += K3_WARPS)
+    if (A.tstatus[gt] & K3_FAR_FLAG) k3f_tile<T, B>(A, c, rv, gt, lane);   // uniform in the warp
+}
+
+template <typename T, int B = 1>
+__device__ __forceinline__ void k3_fused_dispatch(const AssignArgs<T>& A, long long t0,
+                                                  long long t1, unsigned short* s_tab) {
+  if constexpr (B <= NUMARCK_MAX_B) {
+    if (A.g.B == B)
+      k3_fused_part<T, B>(A, t0, t1, s_tab);
+    else
+      k3_fused_dispatch<T, B + 1>(A, t0, t1, s_tab);
+  }
+}
+
+// CTA b of G takes tiles [b NT / G, (b + 1) NT / G) of the list, variable by variable.
+__global__ void __launch_bounds__(K3_THREADS, 1) k3_assign_fused(FusedArgs F) {
+  extern __shared__ __align__(16) unsigned short s_tab[];   // [65536]: index of each code
+  __shared__ AssignArgs<double> s_ad;
+  __shared__ AssignArgs<float> s_af;
+  const long long G = gridDim.x, b = blockIdx.x;
+  const long long lo = (long long)(((__int128)F.NT * b) / G);
+  const long long hi = (long long)(((__int128)F.NT * (b + 1)) / G);
+  if (lo >= hi) return;
+  for (int v = find_var(F.tpre, F.count, lo); v < F.count && F.tpre[v] < hi; ++v) {
+    const long long base = F.tpre[v];
+    const long long t0 = max(lo, base) - base, t1 = min(hi, F.tpre[v + 1]) - base;
+    if (t0 >= t1) continue;
+    const bool f64 = F.vars[v].g.dtype == NUMARCK_F64;
+    __syncthreads();   // the previous part is done with the table and the argument block
+    if (threadIdx.x == 0) {
+      if (f64) s_ad = fused_assign_args<double>(F.vars[v]);
+      else s_af = fused_assign_args<float>(F.vars[v]);
+    }
+    __syncthreads();
+    if (f64)
+      k3_fused_dispatch<double>(s_ad, t0, t1, s_tab);
+    else
+      k3_fused_dispatch<float>(s_af, t0, t1, s_tab);
+  }
+}
+
+// K3b: scan block t of the list (taken in list order from the batch's ticket counter).
+__global__ void __launch_bounds__(SC_THREADS, 1) k3_scan_fused(FusedArgs F) {
+  __shared__ long long s_blk;
+  if (threadIdx.x == 0) s_blk = (long long)atomicAdd(F.ticket, 1u);
+  __syncthreads();
+  const long long t = s_blk;
+  const int v = find_var(F.spre, F.count, t);
+  const FusedVar& V = F.vars[v];
+  const unsigned long long* counts = reinterpret_cast<const unsigned long long*>(V.ws + V.wl.status);
+  k3_scan_block(counts, const_cast<unsigned long long*>(counts) + V.g.nsub, t - F.spre[v], V.g,
+                V.blob, V.g.dtype == NUMARCK_F64 ? 8 : 4);
+}
+
+// K3c: warps over the tiles of the list.
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k3_exact_fused(FusedArgs F) {
+  extern __shared__ __align__(16) unsigned short k3x_list[];
+  const int lane = (int)lane_id();
+  unsigned short* list = k3x_list + (threadIdx.x >> 5) * SUB;
+  const long long W = (long long)gridDim.x * WARPS;
+  for (long long gt = (long long)blockIdx.x * WARPS + (threadIdx.x >> 5); gt < F.NT; gt += W) {
+    const int v = find_var(F.tpre, F.count, gt);
+    const FusedVar& V = F.vars[v];
+    const unsigned short* codes = reinterpret_cast<const unsigned short*>(V.blob + V.code_off);
+    const long long t = gt - F.tpre[v];
+    if (V.g.dtype == NUMARCK_F64)
+      k3x_tile<double>(static_cast<const double*>(V.cur), codes, V.g, V.blob,
+                       k3x_from_codes<double>(V.g, V.blob, V.code_off), t, list, lane);
+    else
+      k3x_tile<float>(static_cast<const float*>(V.cur), codes, V.g, V.blob,
+                      k3x_from_codes<float>(V.g, V.blob, V.code_off), t, list, lane);
+  }
+}
+
+template <int WARPS>
+cudaError_t launch_exact_fused_w(const FusedArgs& F, int sms, cudaStream_t s) {
+  static int occ[64] = {0};
+  const int smem = WARPS * SUB * 2;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int per_sm = dev < 64 ? occ[dev] : 0;
+  if (per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k3_exact_fused<WARPS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_exact_fused<WARPS>, WARPS * 32,
+                                                      smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (dev < 64) occ[dev] = per_sm;
+  }
+  long long blocks = (long long)sms * per_sm;
+  const long long need = (F.NT + WARPS - 1) / WARPS;
+  if (blocks > need) blocks = need;
+  k3_exact_fused<WARPS><<<(int)blocks, WARPS * 32, smem, s>>>(F);
+  return cudaGetLastError();
 }
 
 template <typename T>
@@ -720,6 +901,39 @@ cudaError_t launch_exact(const CompressPlan& P, cudaStream_t s) {
 cudaError_t launch_assign(const CompressPlan& P, cudaStream_t s) {
   return P.g.dtype == NUMARCK_F64 ? launch_assign_t<double>(P, s, P.cd)
                                   : launch_assign_t<float>(P, s, P.cf);
+}
+
+cudaError_t launch_fused_assign(const FusedArgs& F, int sms, cudaStream_t s) {
+  if (F.NT <= 0) return cudaSuccess;
+  static int occ[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int per_sm = dev < 64 ? occ[dev] : 0;
+  if (per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k3_assign_fused,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, K3_SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_assign_fused, K3_THREADS, K3_SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (dev < 64) occ[dev] = per_sm;
+  }
+  long long blocks = (long long)sms * per_sm;
+  const long long need = (F.NT + K3_WARPS - 1) / K3_WARPS;
+  if (blocks > need) blocks = need;
+  k3_assign_fused<<<(int)blocks, K3_THREADS, K3_SMEM, s>>>(F);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fused_offsets(const FusedArgs& F, cudaStream_t s) {
+  if (F.NS <= 0) return cudaSuccess;
+  k3_scan_fused<<<(unsigned)F.NS, SC_THREADS, 0, s>>>(F);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fused_exact(const FusedArgs& F, int sms, cudaStream_t s) {
+  if (F.NT <= 0) return cudaSuccess;
+  return F.exact_warps == 4 ? launch_exact_fused_w<4>(F, sms, s) : launch_exact_fused_w<8>(F, sms, s);
 }
 
 namespace {

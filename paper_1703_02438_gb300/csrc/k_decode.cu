@@ -26,15 +26,16 @@ namespace nmk {
 
 namespace {
 
+// Decodes units u_begin, u_begin + W, ... < u_end (unit u: segment u mod 2^seg_log2 of tile
+// u >> seg_log2), one warp.
 template <typename T, int B>
 __device__ __forceinline__ void decode_tiles(const DecodeArgs& A, const Geometry& g,
-                                             long long n_inc, long long g0, long long g1,
-                                             const T* s_m) {
+                                             long long n_inc, long long u_begin, long long u_end,
+                                             long long W, const T* s_m) {
   using U = typename BitsOf<T>::U;
   using F = typename Field<B>::type;
   constexpr int FB = 4 * B;
   const int lane = (int)lane_id();
-  const int warp = (int)(threadIdx.x >> 5);
   const T* centres = reinterpret_cast<const T*>(A.blob + g.off_centres);
   const int64_t* idx_off = reinterpret_cast<const int64_t*>(A.blob + g.off_idx_off);
   const int64_t* sub_off = reinterpret_cast<const int64_t*>(A.blob + g.off_sub_off);
@@ -45,11 +46,9 @@ __device__ __forceinline__ void decode_tiles(const DecodeArgs& A, const Geometry
   const unsigned lt = lanemask_lt();
 
   const long long seg_lo = A.start, seg_hi = A.start + A.count;
-  const long long W = (long long)gridDim.x * K4_WARPS;
   const int sl = A.seg_log2;                     // units: 2^sl segments per sub-block
   const int seglen = SUB >> sl;
-  const long long u1 = (g1 + 1) << sl;
-  for (long long u = (g0 << sl) + (long long)blockIdx.x * K4_WARPS + warp; u < u1; u += W) {
+  for (long long u = u_begin; u < u_end; u += W) {
     const long long gt = u >> sl;
     const int sbeg = (int)(u & ((1 << sl) - 1)) * seglen;
     const long long q = gt / g.spb, t = gt - q * g.spb;
@@ -120,13 +119,13 @@ __device__ __forceinline__ void decode_tiles(const DecodeArgs& A, const Geometry
 
 template <typename T, int B = 1>
 __device__ __forceinline__ void decode_dispatch(const DecodeArgs& A, const Geometry& g,
-                                                long long n_inc, long long g0, long long g1,
-                                                const T* s_m) {
+                                                long long n_inc, long long u_begin,
+                                                long long u_end, long long W, const T* s_m) {
   if constexpr (B <= NUMARCK_MAX_B) {
     if (g.B == B)
-      decode_tiles<T, B>(A, g, n_inc, g0, g1, s_m);
+      decode_tiles<T, B>(A, g, n_inc, u_begin, u_end, W, s_m);
     else
-      decode_dispatch<T, B + 1>(A, g, n_inc, g0, g1, s_m);
+      decode_dispatch<T, B + 1>(A, g, n_inc, u_begin, u_end, W, s_m);
   }
 }
 
@@ -165,18 +164,137 @@ __global__ void __launch_bounds__(K4_THREADS, 2) k4_decode(DecodeArgs A) {
   if (!s_ok) return;
   const Geometry g = s_g;
   const int nm = min(1 << g.B, DM_SMEM);
+  const long long u0 = (s_g0 << A.seg_log2) + (long long)blockIdx.x * K4_WARPS + (threadIdx.x >> 5);
+  const long long u1 = (s_g1 + 1) << A.seg_log2;
+  const long long W = (long long)gridDim.x * K4_WARPS;
   if (g.dtype == NUMARCK_F64) {
     double* s_m = reinterpret_cast<double*>(s_tab);
     const double* centres = reinterpret_cast<const double*>(A.blob + g.off_centres);
     for (int r = threadIdx.x; r < nm; r += K4_THREADS) s_m[r] = t_add(1.0, centres[r]);
     __syncthreads();   // the only block-wide barrier after the header
-    decode_dispatch<double>(A, g, s_h.n_inc, s_g0, s_g1, s_m);
+    decode_dispatch<double>(A, g, s_h.n_inc, u0, u1, W, s_m);
   } else {
     float* s_m = reinterpret_cast<float*>(s_tab);
     const float* centres = reinterpret_cast<const float*>(A.blob + g.off_centres);
     for (int r = threadIdx.x; r < nm; r += K4_THREADS) s_m[r] = t_add(1.0f, centres[r]);
     __syncthreads();
-    decode_dispatch<float>(A, g, s_h.n_inc, s_g0, s_g1, s_m);
+    decode_dispatch<float>(A, g, s_h.n_inc, u0, u1, W, s_m);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Fused batch (K6): the decompression of every blob of a batch in one launch. The prep kernel
+// (one CTA) validates each blob's header on the device and writes the tile prefix table; the
+// decode kernel's CTA b of G takes tiles [b NT / G, (b + 1) NT / G) of the concatenated list
+// and, per blob part, loads the header and the multiplier table into shared memory and runs the
+// single-blob loop over its tiles with its warps. A blob whose header is invalid (or whose n
+// differs from the item's) contributes no tiles and reports its error in the status word.
+// ---------------------------------------------------------------------------------------
+constexpr int KP_THREADS = 256;
+
+__global__ void __launch_bounds__(KP_THREADS) k4_fused_prep(FusedDecodeArgs D) {
+  __shared__ long long s_sum[KP_THREADS / 32 + 1];
+  __shared__ long long s_base;
+  if (threadIdx.x == 0) { s_base = 0; D.tpre[0] = 0; *D.ticket = 0ull; }
+  __syncthreads();
+  for (int c0 = 0; c0 < D.count; c0 += KP_THREADS) {
+    const int v = c0 + (int)threadIdx.x;
+    long long nsub = 0;
+    if (v < D.count) {
+      numarck_header h;
+      const uint4* src = reinterpret_cast<const uint4*>(D.vars[v].blob);
+      uint4* dst = reinterpret_cast<uint4*>(&h);
+      for (int i = 0; i < NUMARCK_HEADER_BYTES / 16; ++i) dst[i] = src[i];
+      Geometry g{};
+      int rc = check_header(h, &g);
+      if (!rc && h.n != D.vars[v].n) rc = NUMARCK_ERR_INVALID_ARG;
+      if (!rc && ((uintptr_t)D.vars[v].prev | (uintptr_t)D.vars[v].out) %
+                     (h.dtype == NUMARCK_F64 ? 8u : 4u))
+        rc = NUMARCK_ERR_INVALID_ARG;
+      if (rc) {
+        if (D.status) atomicExch(D.status, rc);
+      } else {
+        nsub = g.nsub;
+      }
+    }
+    // inclusive block scan of nsub
+    const int lane = (int)lane_id(), w = (int)(threadIdx.x >> 5);
+    long long inc = nsub;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane == 31) s_sum[w] = inc;
+    __syncthreads();
+    long long before = s_base;
+    for (int i = 0; i < w; ++i) before += s_sum[i];
+    if (v < D.count) D.tpre[v + 1] = before + inc;
+    __syncthreads();
+    if (threadIdx.x == KP_THREADS - 1) s_base = before + inc;
+    __syncthreads();
+  }
+}
+
+// The decode kernel hands out chunks of K4_CHUNK consecutive tiles of the list from a counter
+// (tiles differ in cost by dtype, B and marker density, so a static split would leave CTAs
+// idle); a CTA keeps the header and multiplier table of the blob it last worked on and reloads
+// them only when a chunk starts in another blob.
+constexpr int K4_CHUNK = 4 * K4_WARPS;
+
+__global__ void __launch_bounds__(K4_THREADS, 2) k4_fused(FusedDecodeArgs D) {
+  __shared__ __align__(16) unsigned char s_tab[DM_SMEM * 8];   // multipliers m = 1 + centre
+  __shared__ __align__(16) numarck_header s_h;
+  __shared__ Geometry s_g;
+  __shared__ DecodeArgs s_a;
+  __shared__ long long s_chunk;
+  __shared__ int s_var;
+  const long long NT = D.tpre[D.count];
+  if (threadIdx.x == 0) s_var = -1;
+  for (;;) {
+    __syncthreads();   // the previous chunk is done with the shared state
+    if (threadIdx.x == 0) s_chunk = (long long)atomicAdd(D.ticket, 1ull);
+    __syncthreads();
+    const long long lo = s_chunk * K4_CHUNK;
+    if (lo >= NT) break;
+    const long long hi = min(NT, lo + K4_CHUNK);
+    for (int v = find_var(D.tpre, D.count, lo); v < D.count && D.tpre[v] < hi; ++v) {
+      const long long base = D.tpre[v];
+      const long long t0 = max(lo, base) - base, t1 = min(hi, D.tpre[v + 1]) - base;
+      if (t0 >= t1) continue;
+      if (v != s_var) {
+        __syncthreads();   // every warp is done with the previous blob's tables
+        const FusedDecodeVar& V = D.vars[v];
+        if (threadIdx.x < NUMARCK_HEADER_BYTES / 16)
+          reinterpret_cast<uint4*>(&s_h)[threadIdx.x] =
+              reinterpret_cast<const uint4*>(V.blob)[threadIdx.x];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          check_header(s_h, &s_g);   // valid: the prep kernel gave it tiles
+          s_a = DecodeArgs{V.blob, V.prev, V.out, D.status, 0, V.n, V.n, nullptr, 0, D.seg_log2};
+          s_var = v;   // read again only after the barriers below
+        }
+        __syncthreads();
+        const int nm = min(1 << s_g.B, DM_SMEM);
+        if (s_g.dtype == NUMARCK_F64) {
+          double* s_m = reinterpret_cast<double*>(s_tab);
+          const double* centres = reinterpret_cast<const double*>(V.blob + s_g.off_centres);
+          for (int r = threadIdx.x; r < nm; r += K4_THREADS) s_m[r] = t_add(1.0, centres[r]);
+        } else {
+          float* s_m = reinterpret_cast<float*>(s_tab);
+          const float* centres = reinterpret_cast<const float*>(V.blob + s_g.off_centres);
+          for (int r = threadIdx.x; r < nm; r += K4_THREADS) s_m[r] = t_add(1.0f, centres[r]);
+        }
+        __syncthreads();
+      }
+      const long long u0 = (t0 << D.seg_log2) + (threadIdx.x >> 5), u1 = t1 << D.seg_log2;
+      if (s_g.dtype == NUMARCK_F64)
+        decode_dispatch<double>(s_a, s_g, s_h.n_inc, u0, u1, K4_WARPS,
+                                reinterpret_cast<const double*>(s_tab));
+      else
+        decode_dispatch<float>(s_a, s_g, s_h.n_inc, u0, u1, K4_WARPS,
+                               reinterpret_cast<const float*>(s_tab));
+    }
   }
 }
 
@@ -206,6 +324,25 @@ cudaError_t launch_decode(const DecodePlan& P, cudaStream_t s) {
   DecodeArgs A{P.blob, P.prev_seg, P.out_seg, P.status, P.start, P.count, P.n_expected, P.status2,
                P.dtype, sl};
   k4_decode<<<(int)blocks, K4_THREADS, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fused_decode(const FusedDecodeArgs& D, int sms, cudaStream_t s) {
+  if (D.count <= 0) return cudaSuccess;
+  static int occ[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int per_sm = dev < 64 ? occ[dev] : 0;
+  if (per_sm == 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k4_fused, K4_THREADS, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (dev < 64) occ[dev] = per_sm;
+  }
+  k4_fused_prep<<<1, KP_THREADS, 0, s>>>(D);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k4_fused<<<sms * per_sm, K4_THREADS, 0, s>>>(D);
   return cudaGetLastError();
 }
 

@@ -23,17 +23,6 @@ namespace nmk {
 
 namespace {
 
-template <typename T>
-__device__ __forceinline__ void anchor_min_consts(Consts<T>& c, const Ctrl* ctrl) {
-  const unsigned long long key = ctrl->amin_key;
-  double a = key ? key_to_ratio(key) : 0.0;
-  if (a == 0.0) a = 0.0;  // a zero minimum is taken as +0
-  c.a = (T)a;             // exact: the key was made from a T value
-  c.af = (float)c.a;
-  c.K0 = __fadd_ru(__fmul_ru(__fmul_ru(0x1p-18f, c.inv_wf), fabsf(c.af)), 0x1p-60f);
-  c.C0 = __fmaf_ru(0x1p-22f, fabsf(c.af), __fadd_ru(0x1.8p-49f, 0x1p-100f));
-}
-
 // ---------------------------------------------------------------------------------------
 // K0: per-element exact ratio, binnable test, max of the order key (= min ratio)
 // ---------------------------------------------------------------------------------------
@@ -41,42 +30,15 @@ template <typename T>
 __global__ void __launch_bounds__(512) k0_anchor_min(const T* __restrict__ prev,
                                                      const T* __restrict__ cur, int64_t n,
                                                      Consts<T> c, Ctrl* ctrl) {
-  unsigned long long best = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
-    const T p = ld_stream(prev + j), x = ld_stream(cur + j);
-    const T d = t_sub(x, p);
-    const T r = t_div(d, p);
-    if (t_abs(r) <= c.cap) {
-      const unsigned long long k = min_key(r);
-      best = k > best ? k : best;
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long t = __shfl_xor_sync(0xffffffffu, best, o);
-    best = t > best ? t : best;
-  }
-  if (lane_id() == 0 && best) atomicMax(&ctrl->amin_key, best);
+  k0_publish(k0_range<T>(prev, cur, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, n, stride, c),
+             ctrl);
 }
 
 // ---------------------------------------------------------------------------------------
 // K1
 // ---------------------------------------------------------------------------------------
 constexpr int K1_THREADS = 1024;                // one CTA per SM
-constexpr int K1_UNROLL = 2;                    // 16-byte vectors of each input per lane per step
-constexpr int K1_STAGE = 2 * K1_UNROLL * 32 * 16;   // bytes of a warp's stage (prev, cur)
-
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n"
-               :: "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-}
 
 template <typename T, bool VEC>
 __global__ void __launch_bounds__(K1_THREADS, 1) k1_hist(const T* __restrict__ prev,
@@ -87,11 +49,7 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_hist(const T* __restrict__ p
                                                       unsigned short* codes) {
   extern __shared__ __align__(16) unsigned int sh[];   // K1's window, then the warps' stages
   if (anchor_min) anchor_min_consts<T>(c, ctrl);
-  int c0 = 0;  // bin of a zero change ratio: centre of the shared window
-  if (anchor_min) {
-    const double z = floor(-(double)c.a * (double)c.inv_w);
-    c0 = (int)fmin(fmax(z, 0.0), (double)(1 << (WIN_LOG2 + 1)));
-  }
+  const int c0 = zero_change_bin<T>(c, anchor_min != 0);   // centre of the shared window
   HistCtx h{sh, hist, ctrl, c0 - SH_BINS / 2, c.hbase, c0 - CODE_HALF, codes};
   k1_begin(h, tstatus, nsub);
 
@@ -102,74 +60,10 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_hist(const T* __restrict__ p
 
   if (VEC) {
     using V = Vec<T>;
-    using VT = typename V::type;
-    const VT* pv = reinterpret_cast<const VT*>(prev);
-    const VT* xv = reinterpret_cast<const VT*>(cur);
     const int64_t nvec = n / V::N;
-    // this lane's slots of the warp's stage: [u][lane] prev vectors, then cur vectors; a lane
-    // reads back only what it copied itself
-    VT* sp = reinterpret_cast<VT*>(reinterpret_cast<unsigned char*>(sh + SH_BINS) +
-                                   (threadIdx.x >> 5) * K1_STAGE);
-    VT* sx = sp + K1_UNROLL * 32;
-    const int64_t step = nwarps * (32 * K1_UNROLL);
-    auto stage = [&](int64_t b0) {
-#pragma unroll
-      for (int u = 0; u < K1_UNROLL; ++u) {
-        const int64_t vi = b0 + u * 32 + lane;
-        if (vi < nvec) {
-          cp_async16(sp + u * 32 + lane, pv + vi);
-          cp_async16(sx + u * 32 + lane, xv + vi);
-        }
-      }
-      cp_async_commit();
-    };
-    if (gwarp * (32 * K1_UNROLL) < nvec) stage(gwarp * (32 * K1_UNROLL));
-    for (int64_t base = gwarp * (32 * K1_UNROLL); base < nvec; base += step) {
-      T pe[K1_UNROLL][V::N], xe[K1_UNROLL][V::N];
-      bool ok[K1_UNROLL];
-      cp_async_wait_all();
-#pragma unroll
-      for (int u = 0; u < K1_UNROLL; ++u) {
-        const int64_t vi = base + u * 32 + lane;
-        ok[u] = vi < nvec;
-        VT a = {}, b = {};
-        if (ok[u]) { a = sp[u * 32 + lane]; b = sx[u * 32 + lane]; }
-        V::get(a, pe[u]);
-        V::get(b, xe[u]);
-      }
-      if (base + step < nvec) stage(base + step);   // in flight while this step is classified
-      unsigned pend = 0;   // bit u * V::N + v: element needs the exact sequences
-#pragma unroll
-      for (int u = 0; u < K1_UNROLL; ++u) {
-        const int64_t vi = base + u * 32 + lane;
-        unsigned cw[V::N];
-#pragma unroll
-        for (int v = 0; v < V::N; ++v) {
-          int b = 0;
-          bool pass = false;
-          const int kind = ok[u] ? Classifier<T>::fast(pe[u][v], xe[u][v], c, h.cbase, b, pass) : 0;
-          const bool binned = kind == 1;
-          if (kind >= 2) pend |= 1u << (u * V::N + v);
-          cw[v] = bin_code(h, binned, b, pass);
-          hist_add(h, binned, b, lmin, lmax);
-        }
-        if (ok[u]) reinterpret_cast<typename V::codes*>(codes)[vi] = V::pack(cw);
-      }
-      // settle undecided elements (rare) with the exact sequences, one per lane per round
-      while (__any_sync(0xffffffffu, pend != 0u)) {
-        int b = 0;
-        bool binned = false, pass = false;
-        if (pend) {
-          const int k = __ffs(pend) - 1;
-          pend &= pend - 1;
-          const int u = k / V::N, v = k % V::N;
-          const int64_t j = (base + u * 32 + lane) * V::N + v;   // reloaded: keeps pe, xe short-lived
-          binned = Classifier<T>::exact(prev[j], cur[j], c, h.cbase, b, pass) == 1;
-          codes[j] = (unsigned short)bin_code(h, binned, b, pass);
-        }
-        hist_add(h, binned, b, lmin, lmax);
-      }
-    }
+    unsigned char* stage = reinterpret_cast<unsigned char*>(sh + SH_BINS) +
+                           (threadIdx.x >> 5) * K1_STAGE;
+    k1_vec_range<T>(h, c, prev, cur, 0, nvec, gwarp, nwarps, stage, lmin, lmax);
     // scalar tail (< V elements), one warp
     const int64_t t0 = nvec * V::N;
     if (t0 < n && gwarp == 0) {
@@ -183,29 +77,141 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_hist(const T* __restrict__ p
       hist_add(h, binned, b, lmin, lmax);
     }
   } else {
-    constexpr int U = 8;
-    for (int64_t base = gwarp * (32 * U); base < n; base += nwarps * (32 * U)) {
-      T pe[U], xe[U];
-      bool ok[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int64_t j = base + u * 32 + lane;
-        ok[u] = j < n;
-        pe[u] = ok[u] ? ld_stream(prev + j) : (T)0;
-        xe[u] = ok[u] ? ld_stream(cur + j) : (T)0;
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        int b = 0;
-        bool pass = false;
-        const bool binned = ok[u] && Classifier<T>::exact(pe[u], xe[u], c, h.cbase, b, pass) == 1;
-        if (ok[u]) codes[base + u * 32 + lane] = (unsigned short)bin_code(h, binned, b, pass);
-        hist_add(h, binned, b, lmin, lmax);
-      }
-    }
+    k1_scalar_range<T, 8>(h, c, prev, cur, 0, n, gwarp, nwarps, lmin, lmax);
   }
 
   k1_end(h, lmin, lmax);
+}
+
+// ---------------------------------------------------------------------------------------
+// Fused batch (K6): K0 and K1 of every variable of a batch in one persistent launch each.
+// The work list is the concatenation of the variables' bytes (wpre); CTA b of G takes bytes
+// [b WT / G, (b + 1) WT / G) and, for each variable that range covers, the elements between the
+// two boundaries rounded down to a multiple of 256 (both neighbours round a shared boundary the
+// same way, and a variable's last CTA ends at n). Per variable part (a segment) the CTA clears
+// its shared window, runs the single-variable loop over the part with its warps, and merges the
+// window into that variable's histogram; the part's per-tile counts are cleared on the way.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ Consts<T> fused_consts(const FusedVar& V);
+template <>
+__device__ __forceinline__ Consts<double> fused_consts<double>(const FusedVar& V) { return V.cd; }
+template <>
+__device__ __forceinline__ Consts<float> fused_consts<float>(const FusedVar& V) { return V.cf; }
+
+// Element boundary of work coordinate x inside variable v (see above).
+__device__ __forceinline__ int64_t fused_elem(long long x, long long w_lo, long long w_hi,
+                                              int64_t n, int L) {
+  if (x <= w_lo) return 0;
+  if (x >= w_hi) return n;
+  const int64_t e = ((x - w_lo) / L) & ~(int64_t)255;
+  return e < n ? e : n;
+}
+
+// Calls seg(v, e0, e1) for every variable part of this CTA's work range (uniform in the CTA).
+template <typename Seg>
+__device__ __forceinline__ void fused_parts(const FusedArgs& F, Seg seg) {
+  const long long G = gridDim.x, b = blockIdx.x;
+  const long long lo = (long long)(((__int128)F.WT * b) / G);
+  const long long hi = (long long)(((__int128)F.WT * (b + 1)) / G);
+  if (lo >= hi) return;
+  for (int v = find_var(F.wpre, F.count, lo); v < F.count && F.wpre[v] < hi; ++v) {
+    const long long w_lo = F.wpre[v], w_hi = F.wpre[v + 1];
+    if (w_hi <= w_lo) continue;
+    const FusedVar& V = F.vars[v];
+    const int L = V.g.dtype == NUMARCK_F64 ? 8 : 4;
+    const int64_t e0 = fused_elem(lo, w_lo, w_hi, V.g.n, L);
+    const int64_t e1 = fused_elem(hi, w_lo, w_hi, V.g.n, L);
+    if (e0 < e1) seg(v, V, e0, e1);
+  }
+}
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) k0_fused(FusedArgs F) {
+  fused_parts(F, [&](int, const FusedVar& V, int64_t e0, int64_t e1) {
+    if (V.g.anchor != NUMARCK_ANCHOR_MIN) return;
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(V.ws + V.wl.ctrl);
+    if (V.g.dtype == NUMARCK_F64)
+      k0_publish(k0_range<double>(static_cast<const double*>(V.prev),
+                                  static_cast<const double*>(V.cur), e0 + threadIdx.x, e1,
+                                  THREADS, V.cd), ctrl);
+    else
+      k0_publish(k0_range<float>(static_cast<const float*>(V.prev),
+                                 static_cast<const float*>(V.cur), e0 + threadIdx.x, e1, THREADS,
+                                 V.cf), ctrl);
+  });
+}
+
+template <typename T, int THREADS>
+__device__ __forceinline__ void k1_fused_part(const FusedVar& V, int64_t e0, int64_t e1,
+                                              unsigned int* sh) {
+  Consts<T> c = fused_consts<T>(V);
+  Ctrl* ctrl = reinterpret_cast<Ctrl*>(V.ws + V.wl.ctrl);
+  const bool amin = V.g.anchor == NUMARCK_ANCHOR_MIN;
+  if (amin) anchor_min_consts<T>(c, ctrl);
+  const int c0 = zero_change_bin<T>(c, amin);
+  const int64_t n = V.g.n;
+  HistCtx h{sh, reinterpret_cast<unsigned long long*>(V.ws + V.wl.hist), ctrl, c0 - SH_BINS / 2,
+            c.hbase, c0 - CODE_HALF, reinterpret_cast<unsigned short*>(V.blob + V.code_off)};
+  if (e0 == 0 && threadIdx.x == 0) ctrl->code_base = h.cbase;
+  for (int i = threadIdx.x; i < SH_BINS; i += THREADS) sh[i] = 0u;
+  clear_tile_counts(reinterpret_cast<unsigned long long*>(V.ws + V.wl.status), V.g, e0, e1,
+                    e1 == n);
+  __syncthreads();
+  int lmin = 0x7FFFFFFF, lmax = (int)0x80000000;
+  const int warp = (int)(threadIdx.x >> 5);
+  const T* prev = static_cast<const T*>(V.prev);
+  const T* cur = static_cast<const T*>(V.cur);
+  if (V.aligned16) {
+    using Vv = Vec<T>;
+    const int64_t nvec = n / Vv::N;
+    const int64_t v1 = e1 == n ? nvec : e1 / Vv::N;
+    unsigned char* stage = reinterpret_cast<unsigned char*>(sh + SH_BINS) + warp * K1_STAGE;
+    k1_vec_range<T>(h, c, prev, cur, e0 / Vv::N, v1, warp, THREADS / 32, stage, lmin, lmax);
+    if (e1 == n && nvec * Vv::N < n && warp == 0)
+      k1_scalar_range<T, 1>(h, c, prev, cur, nvec * Vv::N, n, 0, 1, lmin, lmax);
+  } else {
+    k1_scalar_range<T, 8>(h, c, prev, cur, e0, e1, warp, THREADS / 32, lmin, lmax);
+  }
+  k1_end(h, lmin, lmax);
+  __syncthreads();   // the window and k1_end's shared range are reused by the next part
+}
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) k1_fused(FusedArgs F) {
+  extern __shared__ __align__(16) unsigned int sh[];   // the window, then the warps' stages
+  fused_parts(F, [&](int, const FusedVar& V, int64_t e0, int64_t e1) {
+    if (V.g.dtype == NUMARCK_F64)
+      k1_fused_part<double, THREADS>(V, e0, e1, sh);
+    else
+      k1_fused_part<float, THREADS>(V, e0, e1, sh);
+  });
+}
+
+template <int THREADS>
+cudaError_t launch_k1_fused(const FusedArgs& F, int sms, cudaStream_t s) {
+  static int occ[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const size_t smem = SH_BINS * sizeof(unsigned int) + (THREADS / 32) * K1_STAGE;
+  int per_sm = dev < 64 ? occ[dev] : 0;
+  if (per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k1_fused<THREADS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k1_fused<THREADS>, THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (dev < 64) occ[dev] = per_sm;
+  }
+  const int blocks = sms * per_sm;
+  if (F.any_min) {
+    k0_fused<THREADS><<<blocks, THREADS, 0, s>>>(F);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k1_fused<THREADS><<<blocks, THREADS, smem, s>>>(F);
+  return cudaGetLastError();
 }
 
 template <typename T>
@@ -262,6 +268,11 @@ cudaError_t launch_hist_tv(const CompressPlan& P, cudaStream_t s) {
 }
 
 }  // namespace
+
+cudaError_t launch_fused_hist(const FusedArgs& F, int k1_threads, int sms, cudaStream_t s) {
+  if (F.WT <= 0) return cudaSuccess;
+  return k1_threads == 512 ? launch_k1_fused<512>(F, sms, s) : launch_k1_fused<1024>(F, sms, s);
+}
 
 cudaError_t launch_anchor_min(const CompressPlan& P, cudaStream_t s) {
   if (P.g.n == 0) return cudaSuccess;

@@ -48,16 +48,6 @@ struct Stage {
   static constexpr int REGION = std::max(TAB * L + K41_WARPS * BYTES, DM_SMEM * L);
 };
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n"
-               :: "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-}
 
 __device__ __forceinline__ void lds4(const double* p, double* v) {
   const double2 a = reinterpret_cast<const double2*>(p)[0];

@@ -232,7 +232,7 @@ __device__ __forceinline__ T anchor_value(const Ctrl* ctrl, const Consts<T>& c, 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(K2_THREADS, 1) k2_topk(TopkArgs A, Consts<T> c) {
+__device__ __forceinline__ void k2_body(const TopkArgs& A, const Consts<T>& c) {
   __shared__ int s_scan[33];
   __shared__ long long s_ll[33];
   __shared__ unsigned long long s_ull[33];
@@ -382,6 +382,30 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_topk(TopkArgs A, Consts<T> c
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(K2_THREADS, 1) k2_topk(TopkArgs A, Consts<T> c) {
+  k2_body<T>(A, c);
+}
+
+// Fused batch (K6): K2 of every variable of a batch in one launch, CTA v for variable v.
+__global__ void __launch_bounds__(K2_THREADS, 1) k2_fused(FusedArgs F) {
+  const FusedVar& V = F.vars[blockIdx.x];
+  TopkArgs A;
+  A.ctrl = reinterpret_cast<Ctrl*>(V.ws + V.wl.ctrl);
+  A.hist = reinterpret_cast<unsigned long long*>(V.ws + V.wl.hist);
+  A.rank_of = reinterpret_cast<unsigned short*>(V.ws + V.wl.rank);
+  A.selb = reinterpret_cast<int*>(V.ws + V.wl.selb);
+  A.blob = V.blob;
+  A.mtab = V.ws + V.wl.mtab;
+  A.cftab = reinterpret_cast<float*>(V.ws + V.wl.cftab);
+  A.g = V.g;
+  A.hdr = make_header(V.g, V.E, V.block_bytes);
+  if (V.g.dtype == NUMARCK_F64)
+    k2_body<double>(A, V.cd);
+  else
+    k2_body<float>(A, V.cf);
+}
+
 }  // namespace
 
 cudaError_t launch_auto_b(const CompressPlan& P, cudaStream_t s) {
@@ -411,6 +435,12 @@ cudaError_t launch_topk(const CompressPlan& P, cudaStream_t s) {
     k2_topk<double><<<1, K2_THREADS, 0, s>>>(A, P.cd);
   else
     k2_topk<float><<<1, K2_THREADS, 0, s>>>(A, P.cf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fused_topk(const FusedArgs& F, cudaStream_t s) {
+  if (F.count <= 0) return cudaSuccess;
+  k2_fused<<<F.count, K2_THREADS, 0, s>>>(F);
   return cudaGetLastError();
 }
 

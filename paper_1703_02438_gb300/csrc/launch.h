@@ -49,6 +49,65 @@ struct DecodePlan {
   int concurrency;         // decodes expected to share the GPU with this one (0 or 1: none)
 };
 
+// ---- the fused batch (K6): every phase of the compression of all variables of a batch as one
+// persistent launch over a device-side work list, instead of one launch per variable ----
+
+// One variable of a fused batch as the fused kernels read it (device memory, written by the
+// upload kernel from the host plan). Its workspace slice has the single-variable layout wl.
+struct FusedVar {
+  const void* prev;
+  const void* cur;
+  unsigned char* blob;
+  unsigned char* ws;
+  Geometry g;
+  WsLayout wl;
+  double E;
+  int64_t block_bytes;
+  int64_t code_off;
+  int aligned16;
+  int pad;
+  Consts<double> cd;       // valid when g.dtype == F64
+  Consts<float> cf;        // valid when g.dtype == F32
+};
+
+// Work-list prefix tables of a fused batch (device memory, count + 1 entries each): the first
+// K1 work byte, the first 4096-element tile and the first offset-scan block of each variable.
+struct FusedArgs {
+  const FusedVar* vars;
+  const long long* wpre;
+  const long long* tpre;
+  const long long* spre;
+  unsigned int* ticket;    // offset-scan block order (reset by the upload)
+  int count;
+  int any_min;             // some variable uses the MIN grid (K0 runs)
+  long long WT, NT, NS;    // totals of the three tables
+  int exact_warps;         // K3c warps per CTA (4 or 8)
+};
+
+// One blob of a fused decode: what the prep kernel validates and the decode kernel reads.
+struct FusedDecodeVar {
+  const unsigned char* blob;
+  const void* prev;
+  void* out;
+  long long n;
+};
+
+struct FusedDecodeArgs {
+  const FusedDecodeVar* vars;
+  long long* tpre;         // written by the prep kernel: first tile of each blob (count + 1)
+  unsigned long long* ticket;   // chunk counter of the decode kernel (reset by the prep kernel)
+  int32_t* status;
+  int count;
+  int seg_log2;            // each tile is decoded by 2^seg_log2 warps
+};
+
+cudaError_t launch_fused_hist(const FusedArgs& F, int k1_threads, int sms, cudaStream_t s);
+cudaError_t launch_fused_topk(const FusedArgs& F, cudaStream_t s);
+cudaError_t launch_fused_assign(const FusedArgs& F, int sms, cudaStream_t s);
+cudaError_t launch_fused_offsets(const FusedArgs& F, cudaStream_t s);
+cudaError_t launch_fused_exact(const FusedArgs& F, int sms, cudaStream_t s);
+cudaError_t launch_fused_decode(const FusedDecodeArgs& D, int sms, cudaStream_t s);
+
 cudaError_t launch_anchor_min(const CompressPlan& P, cudaStream_t s);  // K0 (ANCHOR_MIN only)
 cudaError_t launch_hist(const CompressPlan& P, cudaStream_t s);        // K1
 cudaError_t launch_auto_b(const CompressPlan& P, cudaStream_t s);      // B from the histogram
@@ -82,5 +141,7 @@ int plan_decompress_check(const void* blob, const void* prev, void* out, int64_t
 int launch_decompress(const void* blob, const void* prev, void* out, int64_t n, int32_t* status,
                       int sms, cudaStream_t s, int concurrency = 1);
 int current_device_sms();
+// Records events[i] of the caller's numarck_trace_events array on s (if set and count >= need).
+void trace_event(int i, int need, cudaStream_t s);
 
 }  // namespace nmk

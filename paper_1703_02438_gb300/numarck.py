@@ -90,6 +90,18 @@ class BatchDecodeItem(ctypes.Structure):
                 ("n", ctypes.c_int64)]
 
 
+class FusedTuning(ctypes.Structure):
+    _fields_ = [("k1_threads", ctypes.c_int32), ("exact_warps", ctypes.c_int32),
+                ("decode_seg_log2", ctypes.c_int32), ("groups", ctypes.c_int32),
+                ("streams", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def fused_tuning(t=(1024, 8, 0, 1, 1)) -> FusedTuning:
+    """(k1_threads, exact_warps, decode_seg_log2[, groups, streams]) as numarck_fused_tuning."""
+    t = tuple(int(v) for v in t) + (1, 1)[max(0, len(t) - 3):]
+    return FusedTuning(t[0], t[1], t[2], t[3], t[4], 0)
+
+
 _lib = None
 
 
@@ -135,6 +147,16 @@ def lib() -> ctypes.CDLL:
         L.numarck_decompress_batch.argtypes = [ctypes.POINTER(BatchDecodeItem), i32, i32, i32, vp,
                                                vp]
         L.numarck_decompress_batch.restype = i32
+        ft = ctypes.POINTER(FusedTuning)
+        L.numarck_fused_workspace_bytes.argtypes = [ctypes.POINTER(BatchItem), i32]
+        L.numarck_fused_workspace_bytes.restype = sz
+        L.numarck_compress_batch_fused.argtypes = [ctypes.POINTER(BatchItem), i32, ft, vp, sz, vp]
+        L.numarck_compress_batch_fused.restype = i32
+        L.numarck_fused_decode_workspace_bytes.argtypes = [i32]
+        L.numarck_fused_decode_workspace_bytes.restype = sz
+        L.numarck_decompress_batch_fused.argtypes = [ctypes.POINTER(BatchDecodeItem), i32, ft, vp,
+                                                     sz, vp, vp]
+        L.numarck_decompress_batch_fused.restype = i32
         L.numarck_compress_noalloc.argtypes = [vp, vp, i64, pp, vp, sz, vp]
         L.numarck_compress_noalloc.restype = i32
         L.numarck_version.argtypes = []
@@ -407,15 +429,24 @@ def selftest_wait(flag: torch.Tensor, limit_ns: int, status: torch.Tensor, strea
 
 
 class Batch:
-    """A fixed list of variables to compress together (see numarck_compress_batch).
+    """A fixed list of variables to compress together.
 
     pairs: list of (prev, cur) 1-D CUDA tensors; specs: list of (E, B) or (E, B, anchor,
     block_bytes) per variable. Blob buffers are allocated once (compress_bound bytes each) and
-    reused by every run, so a run can be captured into a CUDA graph."""
+    reused by every run, so a run can be captured into a CUDA graph.
 
-    def __init__(self, pairs, specs, lanes=8, grid_share=4, workspace=None):
+    Two ways to run it, with the same results: "lanes" (numarck_compress_batch: each variable's
+    kernels, `lanes` variables in flight, grids sized for 1/grid_share of the GPU) and "fused"
+    (numarck_compress_batch_fused: one launch per phase over all variables; `tuning` is
+    (k1_threads, exact_warps, decode_seg_log2, groups, streams)). Each way keeps its own
+    workspace, zero-filled again whenever its layout (the lane count) changes."""
+
+    def __init__(self, pairs, specs, lanes=8, grid_share=4, workspace=None, mode="lanes",
+                 tuning=(1024, 8, 0, 1, 1)):
         self.pairs = [(p.contiguous(), x.contiguous()) for p, x in pairs]
         self.lanes, self.grid_share = int(lanes), int(grid_share)
+        self.mode = mode
+        self.tuning = tuple(tuning)
         arr = (BatchItem * len(pairs))()
         self.blobs = []
         for i, ((p, x), spec) in enumerate(zip(self.pairs, specs)):
@@ -431,22 +462,84 @@ class Batch:
             arr[i] = BatchItem(p.data_ptr(), x.data_ptr(), p.numel(), prm, blob.data_ptr(), bound)
         self.items = arr
         self.count = len(pairs)
-        self.ws = workspace or Workspace(self.pairs[0][0].device if self.pairs else "cuda")
+        dev = self.pairs[0][0].device if self.pairs else "cuda"
+        self.ws = workspace or Workspace(dev)
+        self.fws = Workspace(dev)
+        self.dws = None
+        self._lane_layout = None
 
     def set_lanes(self, lanes, grid_share):
+        self.mode = "lanes"
         self.lanes, self.grid_share = int(lanes), int(grid_share)
+
+    def set_fused(self, tuning=(1024, 8, 0, 1, 1)):
+        self.mode = "fused"
+        self.tuning = tuple(tuning)
+
+    def _tuning(self):
+        return fused_tuning(self.tuning)
 
     def run(self, stream=None):
         """Queues the compression of every variable; returns the list of blob buffers."""
+        if self.mode == "fused":
+            need = int(lib().numarck_fused_workspace_bytes(self.items, self.count))
+            if need == 0 and self.count:
+                raise NumarckError(ERR_INVALID_ARG, "numarck_fused_workspace_bytes")
+            ws = self.fws.get(need, stream)
+            t = self._tuning()
+            _check(lib().numarck_compress_batch_fused(self.items, self.count, ctypes.byref(t),
+                                                      ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                                      ctypes.c_void_p(_stream_ptr(stream))),
+                   "numarck_compress_batch_fused")
+            return self.blobs
         need = int(lib().numarck_batch_workspace_bytes(self.items, self.count, self.lanes))
         if need == 0 and self.count:
             raise NumarckError(ERR_INVALID_ARG, "numarck_batch_workspace_bytes")
+        fresh = self.ws.buf is None or self.ws.buf.numel() < need
         ws = self.ws.get(need, stream)
+        if not fresh and self._lane_layout not in (None, self.lanes):
+            # another lane count placed the lanes' slices elsewhere: start from zero again
+            _check(lib().numarck_workspace_init(ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                                ctypes.c_void_p(_stream_ptr(stream))),
+                   "numarck_workspace_init")
+        self._lane_layout = self.lanes
         _check(lib().numarck_compress_batch(self.items, self.count, self.lanes, self.grid_share,
                                             ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                                             ctypes.c_void_p(_stream_ptr(stream))),
                "numarck_compress_batch")
         return self.blobs
+
+    def decompress(self, prevs, outs=None, status=None, stream=None):
+        """Reconstructs every variable from this batch's blobs, the same way the batch runs."""
+        if self.mode != "fused":
+            return decompress_batch(self.blobs, prevs, outs=outs, lanes=self.lanes,
+                                    grid_share=self.grid_share, status=status, stream=stream)
+        if self.dws is None:
+            nbytes = int(lib().numarck_fused_decode_workspace_bytes(self.count))
+            self.dws = torch.empty(max(nbytes, 256), dtype=torch.uint8,
+                                   device=self.blobs[0].device)
+        return decompress_batch_fused(self.blobs, prevs, outs=outs, tuning=self.tuning,
+                                      workspace=self.dws, status=status, stream=stream)
+
+
+def decompress_batch_fused(blobs, prevs, outs=None, tuning=(1024, 8, 0, 1, 1), workspace=None,
+                           status=None, stream=None):
+    """numarck_decompress_batch_fused: every blob of a batch in one prep and one decode launch."""
+    outs = outs or [torch.empty_like(p) for p in prevs]
+    arr = (BatchDecodeItem * len(blobs))()
+    for i, (b, p, o) in enumerate(zip(blobs, prevs, outs)):
+        arr[i] = BatchDecodeItem(b.data_ptr(), p.data_ptr(), o.data_ptr(), p.numel())
+    if workspace is None:
+        nbytes = int(lib().numarck_fused_decode_workspace_bytes(len(blobs)))
+        workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=blobs[0].device)
+    t = fused_tuning(tuning)
+    sp = ctypes.c_void_p(status.data_ptr()) if status is not None else None
+    _check(lib().numarck_decompress_batch_fused(arr, len(blobs), ctypes.byref(t),
+                                                ctypes.c_void_p(workspace.data_ptr()),
+                                                workspace.numel(), sp,
+                                                ctypes.c_void_p(_stream_ptr(stream))),
+           "numarck_decompress_batch_fused")
+    return outs
 
 
 def decompress_batch(blobs, prevs, outs=None, lanes=8, grid_share=4, status=None, stream=None):

@@ -222,3 +222,44 @@ def test_batch_validation_before_device(lib):
     assert lib.numarck_compress_batch(short, 1, 1, 1, ctypes.c_void_p(A), 1 << 40, None) \
         == N.ERR_CAPACITY
     assert lib.numarck_compress_batch(items, 0, 1, 1, None, 0, None) == N.OK
+
+
+def test_fused_batch_validation_before_device(lib):
+    """The fused batch calls validate the tuning, every item and the workspace on the host
+    before queueing anything."""
+    A = 1 << 20
+    good = N.Params(N.F64, 8, 1e-3, 0, 0, 0)
+    f32 = N.Params(N.F32, 10, 1e-4, 1, 0, 3001)
+    n = 5000
+    items = (N.BatchItem * 3)(N.BatchItem(A, A, n, good, A, N.compress_bound(n, good)),
+                              N.BatchItem(A, A, 3 * n, f32, A, N.compress_bound(3 * n, f32)),
+                              N.BatchItem(A, A, n, N.Params(N.F64, 0, 1e-3, 0, 0, 0), A,
+                                          N.compress_bound(n, good)))
+    need = lib.numarck_fused_workspace_bytes(items, 2)
+    assert need >= N.workspace_bytes(n, good) + N.workspace_bytes(3 * n, f32)
+    assert lib.numarck_fused_workspace_bytes(items, 3) == 0              # automatic B
+    assert lib.numarck_fused_workspace_bytes(items, 0) == 0
+    ws = ctypes.c_void_p(A)
+    for t in ((1000, 8, 0, 1, 1, 0), (1024, 6, 0, 1, 1, 0), (1024, 8, 4, 1, 1, 0),
+              (1024, 8, -1, 1, 1, 0), (0, 0, 0, 0, 0, 1), (1024, 8, 0, 65, 1, 0),
+              (1024, 8, 0, 4, 9, 0), (1024, 8, 0, -1, 1, 0)):
+        tu = N.FusedTuning(*t)
+        assert lib.numarck_compress_batch_fused(items, 2, ctypes.byref(tu), ws, need, None) \
+            == N.ERR_INVALID_ARG, t
+        assert lib.numarck_decompress_batch_fused(None, 0, ctypes.byref(tu), ws, 1 << 20, None,
+                                                  None) in (N.OK, N.ERR_INVALID_ARG)
+    assert lib.numarck_compress_batch_fused(items, 3, None, ws, 1 << 40, None) == N.ERR_INVALID_ARG
+    assert lib.numarck_compress_batch_fused(items, 2, None, ws, need - 1, None) == N.ERR_CAPACITY
+    assert lib.numarck_compress_batch_fused(items, 2, None, ctypes.c_void_p(A + 16), need, None) \
+        == N.ERR_INVALID_ARG                                              # 256-byte alignment
+    short = (N.BatchItem * 1)(N.BatchItem(A, A, n, good, A, N.compress_bound(n, good) - 1))
+    assert lib.numarck_compress_batch_fused(short, 1, None, ws, 1 << 40, None) == N.ERR_CAPACITY
+    assert lib.numarck_compress_batch_fused(items, 0, None, None, 0, None) == N.OK
+    # decode: workspace size and alignment, item pointers
+    dn = lib.numarck_fused_decode_workspace_bytes(4)
+    assert dn >= 4 * 32 + 5 * 8 and lib.numarck_fused_decode_workspace_bytes(0) == 0
+    ditems = (N.BatchDecodeItem * 2)(N.BatchDecodeItem(A, A, A, 100), N.BatchDecodeItem(A + 8, A, A, 100))
+    assert lib.numarck_decompress_batch_fused(ditems, 2, None, ws, 1 << 20, None, None) \
+        == N.ERR_INVALID_ARG                                              # blob not 256-aligned
+    assert lib.numarck_decompress_batch_fused(ditems, 1, None, ws, 8, None, None) \
+        == N.ERR_CAPACITY
