@@ -223,6 +223,32 @@ def cpu_oracle_sample(pair, sample: int):
                           f"E=1e-3 B=8, compress {t1 - t0:.2f}s + decompress {t2 - t1:.2f}s")
 
 
+def cpu_parallel_pair(pair, gpu_blob=None):
+    """The all-cores CPU baseline (oracle/numarck_cpu.c, POSIX threads on every host core this
+    process may use) on the whole pair at E=1e-3, B=8: compress + decompress; returns a dict for
+    the bench line. With gpu_blob (the library's blob of the same pair), also whether the two
+    blobs are byte-identical."""
+    from oracle import cpu_parallel as C
+    C.build()
+    p = pair[0].cpu().numpy()
+    x = pair[1].cpu().numpy()
+    cores = C.threads_available()
+    t0 = time.perf_counter()
+    blob = C.compress(p, x, 1e-3, 8, threads=cores)
+    t1 = time.perf_counter()
+    C.decompress(blob, p, threads=cores)
+    t2 = time.perf_counter()
+    out = {"value": p.size * p.itemsize / (t2 - t0) / 1e9, "unit": "GB/s", "cores": cores,
+           "kind": "parallel C (POSIX threads; chunked ratio/bin pass, per-thread histograms, "
+                   "tiles in parallel)",
+           "sample": f"the whole timestep pair 1->2 ({p.size} float64 elements), E=1e-3 B=8, "
+                     f"compress {t1 - t0:.2f}s + decompress {t2 - t1:.2f}s",
+           "seconds": round(t2 - t0, 2)}
+    if gpu_blob is not None:
+        out["blob_equals_gpu"] = blob == gpu_blob
+    return out
+
+
 def run_reference(args):
     rank, world = _rank_world()
     if rank != 0:
@@ -1080,6 +1106,12 @@ def main():
         gbs, sec, desc = cpu_oracle_sample((xs[1], xs[2]), args.cpu_sample)
         cpu = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc,
                "seconds": round(sec, 2)}
+        if not args.f32 and (_host_mem_available() or 0) > 8 * n * 8:
+            ref = N.compress(xs[1], xs[2], 1e-3, 8)
+            torch.cuda.synchronize()
+            ref_bytes = ref[:N.blob_size(N.header_bytes(ref))].cpu().numpy().tobytes()
+            del ref
+            cpu["all_cores"] = cpu_parallel_pair((xs[1], xs[2]), ref_bytes)
 
     if rank == 0:
         line = {
