@@ -32,6 +32,8 @@ import subprocess
 import sys
 import tempfile
 import time
+import zlib
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -525,7 +527,20 @@ def run_zindex(args):
             N.inflate_index(zbuf, zb, hb, copy, start=start, count=cnt)
             N.decompress_range(copy, p[start: start + cnt], start, cnt, header=hb, out=seg)
         t_part = timed(partial)
+        # the host's zlib (level 6, every index block as one stream) on the same blocks
+        index_host = blob[h["off_index"]: h["off_exact"]].cpu().numpy().tobytes()
+        blocks = [index_host[q * h["block_stride"]:
+                             q * h["block_stride"] + ((min(n, (q + 1) * h["epb"]) - q * h["epb"])
+                                                      * B + 7) // 8]
+                  for q in range(h["nblocks"])]
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(max(1, len(os.sched_getaffinity(0)))) as ex:
+            zl = sum(ex.map(lambda b: len(zlib.compress(b, 6)), blocks))
+        t_zl = time.perf_counter() - t0
+        del index_host, blocks
         rows.append({"E": E, "B": B, "index_bytes": raw, "zindex_bytes": zb,
+                     "host_zlib6_bytes": zl, "host_zlib6_ratio": raw / zl,
+                     "host_zlib6_seconds": round(t_zl, 2),
                      "index_ratio": raw / zb, "deflate_ms": t_def,
                      "deflate_gbs": raw / (t_def / 1e3) / 1e9, "inflate_all_ms": t_inf,
                      "inflate_gbs": raw / (t_inf / 1e3) / 1e9,

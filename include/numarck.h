@@ -458,9 +458,10 @@ const char* numarck_version(void);
  * numarck_deflate_index turns a blob's index section into a container of zlib streams (RFC
  * 1950; DEFLATE data of RFC 1951 that any inflater, e.g. zlib's, reads): one stream per index
  * block holding the block's ceil(count * B / 8) bytes (without the raw blob's 16-byte padding).
- * Inside a stream each 4096-element sub-block is one fixed-Huffman DEFLATE block whose matches
- * stay inside the sub-block, followed by an empty stored block that ends it on a byte boundary,
- * so any sub-block inflates on its own: numarck_inflate_index restores only the sub-blocks that
+ * Inside a stream each 4096-element sub-block is one DEFLATE block whose matches stay inside the
+ * sub-block: dynamic Huffman (the code built from its index block's symbol counts, repeated in
+ * every sub-block's header), fixed Huffman or stored, whichever is smallest; a Huffman block is followed by an empty stored block
+ * that ends it on a byte boundary, so any sub-block inflates on its own: numarck_inflate_index restores only the sub-blocks that
  * cover [start, start + count) into a blob buffer (the raw index section, padding included),
  * which numarck_decompress_range then decodes.
  *
@@ -486,7 +487,8 @@ typedef struct numarck_zindex_header {
 
 /* Bytes a container can need for the blob whose header (host copy) is given; 0 if invalid. */
 size_t numarck_zindex_bound(const void* blob_header_host);
-/* Device workspace bytes numarck_deflate_index needs (80 per sub-block); 0 if invalid. */
+/* Device workspace bytes numarck_deflate_index needs (81 per sub-block and about 3 KB per index
+ * block); 0 if invalid. */
 size_t numarck_zindex_workspace_bytes(const void* blob_header_host);
 /* Deflates the index section of a compressed blob (device, with its header's host copy) into
  * zindex (device, zcap >= numarck_zindex_bound, 256-byte aligned). Asynchronous on stream;

@@ -465,7 +465,7 @@ size_t numarck_zindex_bound(const void* header_host) {
 size_t numarck_zindex_workspace_bytes(const void* header_host) {
   Geometry g;
   if (blob_geometry(header_host, &g)) return 0;
-  return (size_t)std::max<int64_t>(256, g.nsub * (16 + 64));   // see launch_deflate
+  return (size_t)zindex_workspace(g);
 }
 
 int numarck_deflate_index(const void* blob, const void* header_host, void* zindex, size_t zcap,
@@ -476,7 +476,7 @@ int numarck_deflate_index(const void* blob, const void* header_host, void* zinde
   if (rc) return rc;
   if (!blob || !zindex || !ws || !aligned(blob, 256) || !aligned(zindex, 256) || !aligned(ws, 16))
     return NUMARCK_ERR_INVALID_ARG;
-  if (zcap < (size_t)zindex_bound(g) || ws_bytes < (size_t)std::max<int64_t>(256, g.nsub * 16))
+  if (zcap < (size_t)zindex_bound(g) || ws_bytes < (size_t)zindex_workspace(g))
     return NUMARCK_ERR_CAPACITY;
   const int sms = device_sms();
   if (sms <= 0) return NUMARCK_ERR_CUDA;

@@ -115,6 +115,7 @@ cudaError_t launch_auto_b(const CompressPlan& P, cudaStream_t s);      // B from
 // deflate of every index block, inflate of sub-blocks [g0, g1].
 int zindex_layout(const Geometry& g, numarck_zindex_header* zh);
 int64_t zindex_bound(const Geometry& g);
+int64_t zindex_workspace(const Geometry& g);   // device workspace bytes of launch_deflate
 cudaError_t launch_deflate(const unsigned char* blob, const Geometry& g, unsigned char* z,
                            unsigned char* ws, int sms, cudaStream_t s);
 cudaError_t launch_inflate(const unsigned char* z, long long zbytes, unsigned char* blob,

@@ -148,3 +148,32 @@ def test_bulk_inflate_restores_a_large_index():
         lo = h["off_index"] + q * h["block_stride"]
         stream = bytes(z[int(zoff[q]): int(zoff[q + 1])].cpu().numpy().tobytes())
         assert zlib.decompress(stream) == bytes(blob[lo: lo + cnt].cpu().numpy().tobytes())
+
+
+@pytest.mark.parametrize("kind", ["plain", "flash", "climate"])
+def test_ratio_against_host_zlib(kind, record_property):
+    """The container against the host's zlib (level 6) on the same index blocks: the per-sub-block
+    dynamic Huffman codes keep it within a small factor of zlib's size, although every
+    sub-block restarts its code and its matches (for partial decoding)."""
+    p, x, E, B, bb = _case(kind)
+    blob = N.compress(torch.from_numpy(p).to(DEV), torch.from_numpy(x).to(DEV), E, B,
+                      block_bytes=bb)
+    hb = N.header_bytes(blob)
+    h = N.parse_header(hb)
+    z = N.deflate_index(blob, hb)
+    zh = N.zindex_header(z)
+    img = blob.cpu().numpy().tobytes()
+    raw = zl = 0
+    for q in range(h["nblocks"]):
+        cnt = min(h["n"], (q + 1) * h["epb"]) - q * h["epb"]
+        lo = h["off_index"] + q * h["block_stride"]
+        block = img[lo: lo + (cnt * B + 7) // 8]
+        raw += len(block)
+        zl += len(zlib.compress(block, 6))
+    ours = zh["total_bytes"] - zh["off_data"]
+    record_property("index_bytes", raw)
+    record_property("container_bytes", ours)
+    record_property("host_zlib6_bytes", zl)
+    print(f"{kind}: index {raw} bytes, container {ours} ({raw / ours:.2f}x), "
+          f"host zlib -6 {zl} ({raw / zl:.2f}x)")
+    assert ours < raw and ours <= 2 * zl + 64 * h["nsub"]
