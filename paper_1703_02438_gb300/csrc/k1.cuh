@@ -220,6 +220,52 @@ __device__ __forceinline__ void k0_publish(unsigned long long best, Ctrl* ctrl) 
   if (lane_id() == 0 && best) atomicMax(&ctrl->amin_key, best);
 }
 
+// Points the float32 estimate cannot decide (rare) are settled with the exact sequences 32 at a
+// time, one per lane: each warp collects their element indices in its queue in shared memory
+// (PQ_CAP entries) and settles a round whenever 32 are waiting, and the rest at its end, instead
+// of running a round of the exact sequences, with most lanes idle, for every step that has any.
+constexpr int PQ_CAP = 64;
+constexpr int PQ_BYTES = PQ_CAP * 8;
+
+struct PendQueue {
+  unsigned long long* q;   // the warp's slots
+  int n;                   // entries waiting (the same in every lane)
+  // One round: lane l settles entry l (settle(valid, index) is called by every lane).
+  template <typename Settle>
+  __device__ __forceinline__ void round(int cnt, Settle& settle) {
+    const int lane = (int)lane_id();
+    const unsigned long long j = lane < cnt ? q[lane] : 0ull;
+    const int rest = n - cnt;
+    const unsigned long long t = lane < rest ? q[cnt + lane] : 0ull;
+    __syncwarp();
+    if (lane < rest) q[lane] = t;
+    n = rest;
+    __syncwarp();
+    settle(lane < cnt, j);
+  }
+  // Queues the elements whose bit k (k < S) is set in this lane's `bits` (index(k): the
+  // element's index), settling a round whenever 32 are waiting (so at most 63 ever wait).
+  template <int S, typename Index, typename Settle>
+  __device__ __forceinline__ void add(unsigned bits, Index index, Settle& settle) {
+    if (!__any_sync(0xffffffffu, bits != 0u)) return;
+    const int lane = (int)lane_id();
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      const bool mine = (bits >> k) & 1u;
+      const unsigned bal = __ballot_sync(0xffffffffu, mine);
+      if (bal == 0u) continue;
+      if (mine) q[n + __popc(bal & lanemask_lt())] = index(k);
+      n += __popc(bal);
+      __syncwarp();
+      if (n >= 32) round(32, settle);
+    }
+  }
+  template <typename Settle>
+  __device__ __forceinline__ void finish(Settle& settle) {
+    if (n > 0) round(n, settle);
+  }
+};
+
 // K1 over 16-byte vectors [v_lo, v_hi) of one variable (prev and cur 16-byte aligned): warp wid
 // of nw takes the steps starting at v_lo + wid * 32 U, then every nw * 32 U vectors, each step
 // 32 U vectors of both inputs (U = K1_UNROLL, lane l holds vectors u * 32 + l). Each warp copies
@@ -230,7 +276,8 @@ __device__ __forceinline__ void k1_vec_range(const HistCtx& h, const Consts<T>& 
                                              const T* __restrict__ prev,
                                              const T* __restrict__ cur, int64_t v_lo,
                                              int64_t v_hi, int64_t wid, int64_t nw,
-                                             unsigned char* stage, int& lmin, int& lmax) {
+                                             unsigned char* stage, unsigned long long* pq,
+                                             int& lmin, int& lmax) {
   using V = Vec<T>;
   using VT = typename V::type;
   const int lane = (int)lane_id();
@@ -253,6 +300,17 @@ __device__ __forceinline__ void k1_vec_range(const HistCtx& h, const Consts<T>& 
     }
     cp_async_commit();
   };
+  // the exact sequences for an element the estimate left undecided (or for nothing)
+  auto settle = [&](bool valid, unsigned long long j) {
+    int b = 0;
+    bool binned = false, pass = false;
+    if (valid) {
+      binned = Classifier<T>::exact(prev[j], cur[j], c, h.cbase, b, pass) == 1;
+      codes[j] = (unsigned short)bin_code(h, binned, b, pass);
+    }
+    hist_add(h, binned, b, lmin, lmax);
+  };
+  PendQueue Q{pq, 0};
   const int64_t first = v_lo + wid * (32 * K1_UNROLL);
   if (first < v_hi) stage_step(first);
   for (int64_t base = first; base < v_hi; base += step) {
@@ -286,21 +344,15 @@ __device__ __forceinline__ void k1_vec_range(const HistCtx& h, const Consts<T>& 
       }
       if (ok[u]) reinterpret_cast<typename V::codes*>(codes)[vi] = V::pack(cw);
     }
-    // settle undecided elements (rare) with the exact sequences, one per lane per round
-    while (__any_sync(0xffffffffu, pend != 0u)) {
-      int b = 0;
-      bool binned = false, pass = false;
-      if (pend) {
-        const int k = __ffs(pend) - 1;
-        pend &= pend - 1;
-        const int u = k / V::N, v = k % V::N;
-        const int64_t j = (base + u * 32 + lane) * V::N + v;   // reloaded: keeps pe, xe short-lived
-        binned = Classifier<T>::exact(prev[j], cur[j], c, h.cbase, b, pass) == 1;
-        codes[j] = (unsigned short)bin_code(h, binned, b, pass);
-      }
-      hist_add(h, binned, b, lmin, lmax);
-    }
+    // undecided elements (rare) wait for a round of the exact sequences
+    Q.add<K1_UNROLL * V::N>(
+        pend,
+        [&](int k) {
+          return (unsigned long long)((base + (k / V::N) * 32 + lane) * V::N + (k % V::N));
+        },
+        settle);
   }
+  Q.finish(settle);
 }
 
 // K1 over elements [j_lo, j_hi) with scalar loads (any alignment; also the tail after the last

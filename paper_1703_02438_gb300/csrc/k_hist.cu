@@ -62,8 +62,9 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_hist(const T* __restrict__ p
     using V = Vec<T>;
     const int64_t nvec = n / V::N;
     unsigned char* stage = reinterpret_cast<unsigned char*>(sh + SH_BINS) +
-                           (threadIdx.x >> 5) * K1_STAGE;
-    k1_vec_range<T>(h, c, prev, cur, 0, nvec, gwarp, nwarps, stage, lmin, lmax);
+                           (threadIdx.x >> 5) * (K1_STAGE + PQ_BYTES);
+    k1_vec_range<T>(h, c, prev, cur, 0, nvec, gwarp, nwarps, stage,
+                    reinterpret_cast<unsigned long long*>(stage + K1_STAGE), lmin, lmax);
     // scalar tail (< V elements), one warp
     const int64_t t0 = nvec * V::N;
     if (t0 < n && gwarp == 0) {
@@ -166,8 +167,10 @@ __device__ __forceinline__ void k1_fused_part(const FusedVar& V, int64_t e0, int
     using Vv = Vec<T>;
     const int64_t nvec = n / Vv::N;
     const int64_t v1 = e1 == n ? nvec : e1 / Vv::N;
-    unsigned char* stage = reinterpret_cast<unsigned char*>(sh + SH_BINS) + warp * K1_STAGE;
-    k1_vec_range<T>(h, c, prev, cur, e0 / Vv::N, v1, warp, THREADS / 32, stage, lmin, lmax);
+    unsigned char* stage = reinterpret_cast<unsigned char*>(sh + SH_BINS) +
+                           warp * (K1_STAGE + PQ_BYTES);
+    k1_vec_range<T>(h, c, prev, cur, e0 / Vv::N, v1, warp, THREADS / 32, stage,
+                    reinterpret_cast<unsigned long long*>(stage + K1_STAGE), lmin, lmax);
     if (e1 == n && nvec * Vv::N < n && warp == 0)
       k1_scalar_range<T, 1>(h, c, prev, cur, nvec * Vv::N, n, 0, 1, lmin, lmax);
   } else {
@@ -193,7 +196,7 @@ cudaError_t launch_k1_fused(const FusedArgs& F, int sms, cudaStream_t s) {
   static int occ[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
-  const size_t smem = SH_BINS * sizeof(unsigned int) + (THREADS / 32) * K1_STAGE;
+  const size_t smem = SH_BINS * sizeof(unsigned int) + (THREADS / 32) * (K1_STAGE + PQ_BYTES);
   int per_sm = dev < 64 ? occ[dev] : 0;
   if (per_sm == 0) {
     cudaError_t e = cudaFuncSetAttribute(k1_fused<THREADS>,
@@ -243,7 +246,8 @@ cudaError_t launch_hist_tv(const CompressPlan& P, cudaStream_t s) {
   static int occ[64] = {0};   // resident CTAs per SM, per device (0 = not configured yet)
   int dev = 0;
   cudaGetDevice(&dev);
-  const size_t smem = SH_BINS * sizeof(unsigned int) + (VEC ? (K1_THREADS / 32) * K1_STAGE : 0);
+  const size_t smem =
+      SH_BINS * sizeof(unsigned int) + (VEC ? (K1_THREADS / 32) * (K1_STAGE + PQ_BYTES) : 0);
   int per_sm = dev < 64 ? occ[dev] : 0;
   if (per_sm == 0) {
     cudaError_t e = cudaFuncSetAttribute(k1_hist<T, VEC>,

@@ -116,8 +116,9 @@ struct StepArgs {
 template <typename T, int B>
 __device__ __forceinline__ void step_tiles(const DecodeArgs& A, const StepArgs& S,
                                            const Geometry& g, long long n_inc, const T* s_m,
-                                           unsigned char* stages, const Consts<T>& c,
-                                           const HistCtx& h, int& lmin, int& lmax) {
+                                           unsigned char* stages, unsigned long long* pq,
+                                           const Consts<T>& c, const HistCtx& h, int& lmin,
+                                           int& lmax) {
   using U = typename BitsOf<T>::U;
   using F = typename Field<B>::type;
   constexpr int FB = 4 * B;
@@ -136,6 +137,18 @@ __device__ __forceinline__ void step_tiles(const DecodeArgs& A, const StepArgs& 
   T* out = static_cast<T*>(A.out_seg);
   const T* cur = static_cast<const T*>(S.cur);
   const unsigned lt = lanemask_lt();
+  // the exact sequences for a point the estimate left undecided: its reconstruction is read back
+  // from the output (written by a lane of this warp before the point was queued)
+  auto settle = [&](bool valid, unsigned long long j) {
+    int b = 0;
+    bool binned = false, pass = false;
+    if (valid) {
+      binned = Classifier<T>::exact(out[j], cur[j], c, h.cbase, b, pass) == 1;
+      S.codes[j] = (unsigned short)bin_code(h, binned, b, pass);
+    }
+    hist_add(h, binned, b, lmin, lmax);
+  };
+  PendQueue Q{pq + (threadIdx.x >> 5) * PQ_CAP, 0};
 
   const long long W = (long long)gridDim.x * K41_WARPS;
   const int sl = A.seg_log2;                     // units: 2^sl segments per sub-block
@@ -235,44 +248,36 @@ __device__ __forceinline__ void step_tiles(const DecodeArgs& A, const StepArgs& 
         for (int k = 0; k < 4; ++k)
           if (e0 + k < cnt) ct[e0 + k] = (unsigned short)cw[k];
       }
-      // undecided points (rare): the exact sequences, one per lane per round; the point's
-      // reconstruction is read back from this lane's own store
-      while (__any_sync(0xffffffffu, pend != 0u)) {
-        int b = 0;
-        bool binned = false, pass = false;
-        if (pend) {
-          const int k = __ffs(pend) - 1;
-          pend &= pend - 1;
-          binned = Classifier<T>::exact(ot[e0 + k], xt[e0 + k], c, h.cbase, b, pass) == 1;
-          ct[e0 + k] = (unsigned short)bin_code(h, binned, b, pass);
-        }
-        hist_add(h, binned, b, lmin, lmax);
-      }
+      // undecided points (rare) wait for a round of the exact sequences
+      Q.add<4>(pend, [&](int k) { return (unsigned long long)(j0 + e0 + k); }, settle);
     }
     if (send == cnt && lane == 0) {             // this warp ends the tile: all its markers seen
       const long long next = (gt + 1 < g.nsub) ? sub_off[gt + 1] : n_inc;
       if (run != next) report(A, NUMARCK_ERR_CORRUPT);
     }
   }
+  Q.finish(settle);
 }
 
 template <typename T, int B = 1>
 __device__ __forceinline__ void step_dispatch(const DecodeArgs& A, const StepArgs& S,
                                               const Geometry& g, long long n_inc, const T* s_m,
-                                              unsigned char* stages, const Consts<T>& c,
-                                              const HistCtx& h, int& lmin, int& lmax) {
+                                              unsigned char* stages, unsigned long long* pq,
+                                              const Consts<T>& c, const HistCtx& h, int& lmin,
+                                              int& lmax) {
   if constexpr (B <= NUMARCK_MAX_B) {
     if (g.B == B)
-      step_tiles<T, B>(A, S, g, n_inc, s_m, stages, c, h, lmin, lmax);
+      step_tiles<T, B>(A, S, g, n_inc, s_m, stages, pq, c, h, lmin, lmax);
     else
-      step_dispatch<T, B + 1>(A, S, g, n_inc, s_m, stages, c, h, lmin, lmax);
+      step_dispatch<T, B + 1>(A, S, g, n_inc, s_m, stages, pq, c, h, lmin, lmax);
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(K41_THREADS, 1) k41_step(DecodeArgs A, StepArgs S, Consts<T> c) {
   extern __shared__ __align__(16) unsigned int sh[];             // K1's shared window, then
-  unsigned char* region = reinterpret_cast<unsigned char*>(sh + SH_BINS);   // Stage's region
+  unsigned char* region = reinterpret_cast<unsigned char*>(sh + SH_BINS);   // Stage's region,
+                                                                   // then the warps' queues
   __shared__ __align__(16) numarck_header s_h;
   __shared__ Geometry s_g;
   __shared__ int s_rc;
@@ -306,8 +311,9 @@ __global__ void __launch_bounds__(K41_THREADS, 1) k41_step(DecodeArgs A, StepArg
     const T* centres = reinterpret_cast<const T*>(A.blob + g.off_centres);
     for (int r = threadIdx.x; r < nm; r += K41_THREADS) s_m[r] = t_add((T)1, centres[r]);
     __syncthreads();
-    step_dispatch<T>(A, S, g, s_h.n_inc, s_m, region + Stage<T>::TAB * sizeof(T), c, h, lmin,
-                     lmax);
+    step_dispatch<T>(A, S, g, s_h.n_inc, s_m, region + Stage<T>::TAB * sizeof(T),
+                     reinterpret_cast<unsigned long long*>(region + Stage<T>::REGION), c, h,
+                     lmin, lmax);
   }
   k1_end(h, lmin, lmax);
 }
@@ -317,7 +323,7 @@ cudaError_t launch_step_t(const DecodePlan& D, const CompressPlan& P, cudaStream
   static int occ[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
-  const size_t smem = SH_BINS * sizeof(unsigned int) + Stage<T>::REGION;
+  const size_t smem = SH_BINS * sizeof(unsigned int) + Stage<T>::REGION + K41_WARPS * PQ_BYTES;
   int per_sm = dev < 64 ? occ[dev] : 0;
   if (per_sm == 0) {
     cudaError_t e = cudaFuncSetAttribute(k41_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
