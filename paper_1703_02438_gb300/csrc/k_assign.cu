@@ -243,16 +243,21 @@ __device__ __forceinline__ void shifted_codes(const unsigned (&win)[NW + 4], int
 // per lane (a tile that starts off a 16-byte boundary funnel-shifts each lane's words with the
 // next lane's). Lanes past the tile end, or whose codes would reach past the codes array, read
 // their codes one by one.
+// One tile gt (one warp): its packed indices, its incompressible flags as half-ballot words into
+// `halves` (u16 h: points 16 h .. 16 h + 15 of the tile; the tile's own code area, or any other
+// 512-byte buffer), and the return value: the tile's incompressible count, with K3_FAR_FLAG when
+// points outside the code window need K3f.
 template <int B, typename T>
-__device__ __forceinline__ void k3a_tiles(const AssignArgs<T>& A, const unsigned short* s_tab,
-                                          long long gt_begin, long long gt_end, long long W,
-                                          int lane, int any) {
+__device__ __forceinline__ unsigned long long k3a_tile(const AssignArgs<T>& A,
+                                                       const unsigned short* s_tab, long long gt,
+                                                       int lane, int any,
+                                                       unsigned short* halves) {
   constexpr unsigned M = (1u << B) - 1u;
   constexpr bool kSentinel = B < 16;             // see k3_assign
   constexpr int EL = B % 2 == 0 ? 16 : 32, NW = EL / 2, NV = EL / 8, WL = EL * B / 32;
   constexpr int SEGW = 32 * EL;
   const Geometry& g = A.g;
-  for (long long gt = gt_begin; gt < gt_end; gt += W) {
+  {
     const TileRef tr = tile_ref<B>(g, gt, A.blob, A.codes);
     const int cnt = tr.cnt;
     const int sh = (int)(tr.j0 & 7);
@@ -321,7 +326,7 @@ __device__ __forceinline__ void k3a_tiles(const AssignArgs<T>& A, const unsigned
       }
 #pragma unroll
       for (int h = 0; h < EL / 16; ++h)
-        if (e0 + 16 * h < cnt) tr.halves[(e0 >> 4) + h] = (unsigned short)(fl >> (16 * h));
+        if (e0 + 16 * h < cnt) halves[(e0 >> 4) + h] = (unsigned short)(fl >> (16 * h));
       count += __popc(fl);
       const int ow = (sb0 / SEGW) * (32 * WL) + lane * WL;   // first word of the lane's fields
       if (ow < tr.twords) {
@@ -342,7 +347,19 @@ __device__ __forceinline__ void k3a_tiles(const AssignArgs<T>& A, const unsigned
     }
     count = __reduce_add_sync(0xffffffffu, count);
     const bool fix = any && __any_sync(0xffffffffu, kSentinel ? far > M : far != 0u);
-    if (lane == 0) A.tstatus[gt] = (unsigned long long)count | (fix ? K3_FAR_FLAG : 0ull);
+    return (unsigned long long)count | (fix ? K3_FAR_FLAG : 0ull);
+  }
+}
+
+template <int B, typename T>
+__device__ __forceinline__ void k3a_tiles(const AssignArgs<T>& A, const unsigned short* s_tab,
+                                          long long gt_begin, long long gt_end, long long W,
+                                          int lane, int any) {
+  for (long long gt = gt_begin; gt < gt_end; gt += W) {
+    // the flags go over the tile's own, already consumed codes
+    unsigned short* own = tile_ref<B>(A.g, gt, A.blob, A.codes).halves;
+    const unsigned long long st = k3a_tile<B>(A, s_tab, gt, lane, any, own);
+    if (lane == 0) A.tstatus[gt] = st;
   }
 }
 
@@ -383,12 +400,15 @@ __global__ void __launch_bounds__(K3_THREADS, 1) k3_assign(AssignArgs<T> A) {
 // bins from the zero-change bin). Each such tile is indexed again from prev and cur with the
 // exact sequences (bin, rank, check of §III.C against the selected centre), replacing K3a's
 // image, ballots and count. The tile's codes are not used (K3a has written ballots over them).
-// K3f's work on one flagged tile gt (one warp).
+// K3f's work on one flagged tile gt (one warp): the tile's image, its half-ballots (into `halves`,
+// or its code area when null) and, returned, its incompressible count.
 template <typename T, int B>
-__device__ __forceinline__ void k3f_tile(const AssignArgs<T>& A, const Consts<T>& c,
-                                         const RankView& rv, long long gt, int lane) {
+__device__ __forceinline__ int k3f_tile(const AssignArgs<T>& A, const Consts<T>& c,
+                                        const RankView& rv, long long gt, int lane,
+                                        unsigned short* halves = nullptr) {
   constexpr unsigned M = (1u << B) - 1u;
   const TileRef tr = tile_ref<B>(A.g, gt, A.blob, A.codes);
+  if (!halves) halves = tr.halves;
   int count = 0;
   for (int sb0 = 0; sb0 < tr.cnt; sb0 += K3_SEG) {
     unsigned idx[4];
@@ -399,10 +419,10 @@ __device__ __forceinline__ void k3f_tile(const AssignArgs<T>& A, const Consts<T>
       idx[k] = e < tr.cnt ? FarAssigner<T>::index(A.prev[j], A.cur[j], c, rv, A.mtab, A.cftab, M)
                           : M;
     }
-    step_out<B>(idx, sb0, tr.cnt, lane, tr.halves, tr.tw, tr.twords, count);
+    step_out<B>(idx, sb0, tr.cnt, lane, halves, tr.tw, tr.twords, count);
   }
   count = __reduce_add_sync(0xffffffffu, count);
-  if (lane == 0) A.tstatus[gt] = (unsigned long long)count;
+  return count;
 }
 
 template <typename T, int B>
@@ -418,7 +438,8 @@ __global__ void __launch_bounds__(K3_THREADS) k3_fixup(AssignArgs<T> A) {
   for (long long gt = (long long)blockIdx.x * K3_WARPS + (threadIdx.x >> 5); gt < g.nsub;
        gt += W) {
     if (!(A.tstatus[gt] & K3_FAR_FLAG)) continue;   // uniform across the warp
-    k3f_tile<T, B>(A, c, rv, gt, lane);
+    const int count = k3f_tile<T, B>(A, c, rv, gt, lane);
+    if (lane == 0) A.tstatus[gt] = (unsigned long long)count;
   }
 }
 
@@ -699,8 +720,11 @@ __device__ __forceinline__ void k3_fused_part(const AssignArgs<T>& A, long long 
   Consts<T> c = A.c;
   anchor_consts<T>(c, A.g, A.ctrl);
   const RankView rv{A.rank_of, c.hbase, A.ctrl->sel_lo, A.ctrl->sel_hi, M};
-  for (long long gt = t0 + warp; gt < t1; gt += K3_WARPS)
-    if (A.tstatus[gt] & K3_FAR_FLAG) k3f_tile<T, B>(A, c, rv, gt, lane);   // uniform in the warp
+  for (long long gt = t0 + warp; gt < t1; gt += K3_WARPS) {
+    if (!(A.tstatus[gt] & K3_FAR_FLAG)) continue;                          // uniform in the warp
+    const int count = k3f_tile<T, B>(A, c, rv, gt, lane);
+    if (lane == 0) A.tstatus[gt] = (unsigned long long)count;
+  }
 }
 
 template <typename T, int B = 1>
