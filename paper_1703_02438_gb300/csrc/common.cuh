@@ -460,7 +460,8 @@ __device__ __forceinline__ bool check_f64(double p, double x, double m, float cf
 // below into one per-bin term and one term in |Df| (each rounded upward, so every comparison
 // implies the one it replaces).
 // Returns 0 (not binnable), 1 (bin, and pass when the bin is in the window, decided),
-// 2 (the bin needs the exact sequence), 3 (the bin is decided, the check needs the exact one).
+// 2 (the exact sequences must decide: the bin is undecided, or the inputs lie outside the
+// estimate's range), 3 (the bin is decided, the check needs the exact one).
 __device__ __forceinline__ int classify_check_f64_fast(double p, double x, const Consts<double>& c,
                                                        int cbase, int& b, bool& pass) {
   // computed without branches: every quantity below is harmless for any input bits, and the
@@ -495,10 +496,9 @@ __device__ __forceinline__ int classify_check_f64_fast(double p, double x, const
   const bool sure = aD <= c.cap_lo && lo == hi && lo < 4194304.0f;       // bin decided
   const bool outside = (unsigned)(b - cbase) >= (unsigned)CODE_BINS;     // no check needed
   const bool decided = (unsigned)(ex - 100) <= 1840u && (yes || no);     // check decided
-  // p = +-0 (ratio +-inf or NaN) or a non-finite input: not binnable
-  const bool never = ((ph << 1) == 0u && pl == 0u) || ep == 0x7FF || ex == 0x7FF;
-  return in_range ? (beyond ? 0 : (!sure ? 2 : ((outside || decided) ? 1 : 3)))
-                  : (never ? 0 : 2);
+  // outside the estimate's range (p = +-0, subnormal or huge, a non-finite input) the exact
+  // sequences decide: such points are rare, and the callers settle them 32 at a time
+  return in_range ? (beyond ? 0 : (!sure ? 2 : ((outside || decided) ? 1 : 3))) : 2;
 }
 
 // ------------------------------------------------------------------------------------------
