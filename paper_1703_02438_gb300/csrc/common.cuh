@@ -459,9 +459,8 @@ __device__ __forceinline__ bool check_f64(double p, double x, double m, float cf
 // with G = fl(cfe - Df) and delta + Kc is exact. The terms of delta + Kc and dH are regrouped
 // below into one per-bin term and one term in |Df| (each rounded upward, so every comparison
 // implies the one it replaces).
-// Returns 0 (not binnable), 1 (bin, and pass when the bin is in the window, decided),
-// 2 (the exact sequences must decide: the bin is undecided, or the inputs lie outside the
-// estimate's range), 3 (the bin is decided, the check needs the exact one).
+// Returns 1 (binnable: the bin, and pass when the bin is in the window, decided) or 2 (the exact
+// sequences must decide the point).
 __device__ __forceinline__ int classify_check_f64_fast(double p, double x, const Consts<double>& c,
                                                        int cbase, int& b, bool& pass) {
   // computed without branches: every quantity below is harmless for any input bits, and the
@@ -492,13 +491,15 @@ __device__ __forceinline__ int classify_check_f64_fast(double p, double x, const
   const bool no = __fmul_rd(aG, 0x1.fffffcp-1f) > __fmaf_ru(H, 0x1.000008p+0f, T1);
   pass = yes;
   const bool in_range = (unsigned)(ep - 200) <= 1740u && ex != 0x7FF;   // estimate valid
-  const bool beyond = !est || aD > c.cap_hi;                             // |ratio| > cap surely
-  const bool sure = aD <= c.cap_lo && lo == hi && lo < 4194304.0f;       // bin decided
+  // binnable with its bin decided: the estimate is valid and finite, certainly within the cap,
+  // and both ends of its error interval fall in one bin
+  const bool sure = in_range && est && aD <= c.cap_lo && lo == hi && lo < 4194304.0f;
   const bool outside = (unsigned)(b - cbase) >= (unsigned)CODE_BINS;     // no check needed
   const bool decided = (unsigned)(ex - 100) <= 1840u && (yes || no);     // check decided
-  // outside the estimate's range (p = +-0, subnormal or huge, a non-finite input) the exact
-  // sequences decide: such points are rare, and the callers settle them 32 at a time
-  return in_range ? (beyond ? 0 : (!sure ? 2 : ((outside || decided) ? 1 : 3))) : 2;
+  // everything else (inputs outside the estimate's range, ratios near or beyond the cap, bins
+  // or checks the estimate cannot decide) is rare and goes to the exact sequences, which the
+  // callers settle 32 at a time
+  return (sure && (outside || decided)) ? 1 : 2;
 }
 
 // ------------------------------------------------------------------------------------------
