@@ -305,8 +305,8 @@ __device__ __forceinline__ unsigned long long k3a_tile(const AssignArgs<T>& A,
 #pragma unroll
       for (int i = 0; i < WL; ++i) w[i] = 0u;
       unsigned fl = 0;
-#pragma unroll
-      for (int k = 0; k < EL; ++k) {
+      // the lane's EL points: their table entries, flags and fields (disjoint, so added)
+      auto point = [&](int k, bool in) {
         const unsigned code = (cw[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
         const unsigned r = s_tab[code];
         unsigned idx;
@@ -317,12 +317,18 @@ __device__ __forceinline__ unsigned long long k3a_tile(const AssignArgs<T>& A,
           far |= code == CODE_FAR ? 1u : 0u;
           idx = r;
         }
-        const bool in = e0 + k < cnt;
         fl |= (in && idx == M) ? (1u << k) : 0u;
         idx = in ? idx : 0u;                     // zero fields past the tile end
         const int bit = k * B;
-        w[bit >> 5] |= idx << (bit & 31);
-        if ((bit & 31) + B > 32) w[(bit >> 5) + 1] |= idx >> (32 - (bit & 31));
+        w[bit >> 5] += idx << (bit & 31);
+        if ((bit & 31) + B > 32) w[(bit >> 5) + 1] += idx >> (32 - (bit & 31));
+      };
+      if (inside) {                              // every point of the lane lies in the tile
+#pragma unroll
+        for (int k = 0; k < EL; ++k) point(k, true);
+      } else {
+#pragma unroll
+        for (int k = 0; k < EL; ++k) point(k, e0 + k < cnt);
       }
 #pragma unroll
       for (int h = 0; h < EL / 16; ++h)
