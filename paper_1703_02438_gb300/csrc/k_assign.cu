@@ -250,7 +250,7 @@ __device__ __forceinline__ void shifted_codes(const unsigned (&win)[NW + 4], int
 template <int B, typename T>
 __device__ __forceinline__ unsigned long long k3a_tile(const AssignArgs<T>& A,
                                                        const unsigned short* s_tab, long long gt,
-                                                       int lane, int any,
+                                                       int lane, int any, bool far_chk,
                                                        unsigned short* halves) {
   constexpr unsigned M = (1u << B) - 1u;
   constexpr bool kSentinel = B < 16;             // see k3_assign
@@ -306,16 +306,18 @@ __device__ __forceinline__ unsigned long long k3a_tile(const AssignArgs<T>& A,
       for (int i = 0; i < WL; ++i) w[i] = 0u;
       unsigned fl = 0;
       // the lane's EL points: their table entries, flags and fields (disjoint, so added)
-      auto point = [&](int k, bool in) {
+      // (chk false: no point of the variable has CODE_FAR, so every entry read is at most M)
+      auto point = [&](int k, bool in, bool chk) {
         const unsigned code = (cw[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
         const unsigned r = s_tab[code];
-        unsigned idx;
-        if constexpr (kSentinel) {
-          far = max(far, r);
-          idx = min(r, M);
-        } else {
-          far |= code == CODE_FAR ? 1u : 0u;
-          idx = r;
+        unsigned idx = r;
+        if (chk) {
+          if constexpr (kSentinel) {
+            far = max(far, r);
+            idx = min(r, M);
+          } else {
+            far |= code == CODE_FAR ? 1u : 0u;
+          }
         }
         fl |= (in && idx == M) ? (1u << k) : 0u;
         idx = in ? idx : 0u;                     // zero fields past the tile end
@@ -323,12 +325,15 @@ __device__ __forceinline__ unsigned long long k3a_tile(const AssignArgs<T>& A,
         w[bit >> 5] += idx << (bit & 31);
         if ((bit & 31) + B > 32) w[(bit >> 5) + 1] += idx >> (32 - (bit & 31));
       };
-      if (inside) {                              // every point of the lane lies in the tile
+      if (inside && !far_chk) {                  // every point of the lane lies in the tile
 #pragma unroll
-        for (int k = 0; k < EL; ++k) point(k, true);
+        for (int k = 0; k < EL; ++k) point(k, true, false);
+      } else if (inside) {
+#pragma unroll
+        for (int k = 0; k < EL; ++k) point(k, true, true);
       } else {
 #pragma unroll
-        for (int k = 0; k < EL; ++k) point(k, e0 + k < cnt);
+        for (int k = 0; k < EL; ++k) point(k, e0 + k < cnt, true);
       }
 #pragma unroll
       for (int h = 0; h < EL / 16; ++h)
@@ -357,14 +362,23 @@ __device__ __forceinline__ unsigned long long k3a_tile(const AssignArgs<T>& A,
   }
 }
 
+// Whether K3a must look for CODE_FAR points: unless every binnable point's bin (the range K2
+// recorded) lies in K1's code window, or when nothing is binnable (K2 found none, or reported
+// an error).
+__device__ __forceinline__ bool far_check(const Ctrl* ctrl, int any) {
+  const int cb = ctrl->code_base;
+  return !any || ctrl->sel_bmin < cb || ctrl->sel_bmax - cb >= CODE_BINS;
+}
+
 template <int B, typename T>
 __device__ __forceinline__ void k3a_tiles(const AssignArgs<T>& A, const unsigned short* s_tab,
                                           long long gt_begin, long long gt_end, long long W,
                                           int lane, int any) {
+  const bool chk = far_check(A.ctrl, any);
   for (long long gt = gt_begin; gt < gt_end; gt += W) {
     // the flags go over the tile's own, already consumed codes
     unsigned short* own = tile_ref<B>(A.g, gt, A.blob, A.codes).halves;
-    const unsigned long long st = k3a_tile<B>(A, s_tab, gt, lane, any, own);
+    const unsigned long long st = k3a_tile<B>(A, s_tab, gt, lane, any, chk, own);
     if (lane == 0) A.tstatus[gt] = st;
   }
 }
