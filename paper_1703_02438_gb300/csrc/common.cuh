@@ -299,6 +299,9 @@ __host__ __device__ __forceinline__ double key_to_ratio(unsigned long long key) 
 // ------------------------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ int classify_exact(T p, T x, const Consts<T>& c, int& b) {
+  // p = +-0 makes the ratio +-inf or NaN, which is never binnable: decided before the divide,
+  // whose IEEE special-operand path is slow and diverges the warp
+  if (p == (T)0) return 0;
   T d = t_sub(x, p);
   T r = t_div(d, p);
   if (!(t_abs(r) <= c.cap)) return 0;
@@ -459,8 +462,10 @@ __device__ __forceinline__ bool check_f64(double p, double x, double m, float cf
 // with G = fl(cfe - Df) and delta + Kc is exact. The terms of delta + Kc and dH are regrouped
 // below into one per-bin term and one term in |Df| (each rounded upward, so every comparison
 // implies the one it replaces).
-// Returns 1 (binnable: the bin, and pass when the bin is in the window, decided) or 2 (the exact
-// sequences must decide the point).
+// Returns 1 (binnable: the bin, and pass when the bin is in the window, decided), 0 (with
+// ZERO_P: p = +-0, whose ratio is +-inf or NaN and never binnable) or 2 (the exact sequences must
+// decide the point; p = +-0 too without ZERO_P).
+template <bool ZERO_P = true>
 __device__ __forceinline__ int classify_check_f64_fast(double p, double x, const Consts<double>& c,
                                                        int cbase, int& b, bool& pass) {
   // computed without branches: every quantity below is harmless for any input bits, and the
@@ -499,7 +504,12 @@ __device__ __forceinline__ int classify_check_f64_fast(double p, double x, const
   // everything else (inputs outside the estimate's range, ratios near or beyond the cap, bins
   // or checks the estimate cannot decide) is rare and goes to the exact sequences, which the
   // callers settle 32 at a time
-  return (sure && (outside || decided)) ? 1 : 2;
+  if constexpr (ZERO_P) {
+    const bool pzero = ((ph << 1) | pl) == 0u;                         // ratio +-inf or NaN
+    return (sure && (outside || decided)) ? 1 : (pzero ? 0 : 2);
+  } else {
+    return (sure && (outside || decided)) ? 1 : 2;
+  }
 }
 
 // ------------------------------------------------------------------------------------------

@@ -64,8 +64,11 @@ struct Classifier;
 
 // fast(): 0 (not binnable), 1 (bin in b; pass = the own-bin check when b is in the code window)
 // or 2/3 (undecided: call exact()). exact() decides both with the exact T sequences.
+// (ZERO_P: the float64 estimate decides p = +-0 itself rather than leaving it to exact(); K1 takes
+// it, K41 does not: there the test cost more issue slots than the queued zeros.)
 template <>
 struct Classifier<float> {
+  template <bool ZERO_P = true>
   __device__ __forceinline__ static int fast(float p, float x, const Consts<float>& c, int cbase,
                                              int& b, bool& pass) {
     return exact(p, x, c, cbase, b, pass);
@@ -80,9 +83,10 @@ struct Classifier<float> {
 };
 template <>
 struct Classifier<double> {
+  template <bool ZERO_P = true>
   __device__ __forceinline__ static int fast(double p, double x, const Consts<double>& c,
                                              int cbase, int& b, bool& pass) {
-    return classify_check_f64_fast(p, x, c, cbase, b, pass);
+    return classify_check_f64_fast<ZERO_P>(p, x, c, cbase, b, pass);
   }
   __device__ static int exact(double p, double x, const Consts<double>& c, int cbase, int& b,
                               bool& pass) {
@@ -200,6 +204,7 @@ __device__ __forceinline__ unsigned long long k0_range(const T* __restrict__ pre
   unsigned long long best = 0;
   for (int64_t j = j0; j < j1; j += stride) {
     const T p = ld_stream(prev + j), x = ld_stream(cur + j);
+    if (p == (T)0) continue;   // +-inf or NaN: never binnable (and a slow divide)
     const T d = t_sub(x, p);
     const T r = t_div(d, p);
     if (t_abs(r) <= c.cap) {

@@ -235,7 +235,8 @@ __device__ __forceinline__ void step_tiles(const DecodeArgs& A, const StepArgs& 
       for (int k = 0; k < 4; ++k) {
         int b = 0;
         bool pass = false;
-        const int kind = e0 + k < cnt ? Classifier<T>::fast(r[k], xv[k], c, h.cbase, b, pass) : 0;
+        const int kind =
+            e0 + k < cnt ? Classifier<T>::template fast<false>(r[k], xv[k], c, h.cbase, b, pass) : 0;
         const bool binned = kind == 1;
         if (kind >= 2) pend |= 1u << k;
         cw[k] = bin_code(h, binned, b, pass);

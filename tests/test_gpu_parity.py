@@ -166,6 +166,26 @@ def test_adversarial_edges_and_specials(T, anchor):
     check_pair(p, x, E, 9, anchor=anchor, ranges=[(0, 50_000), (3, 4000)])
 
 
+@pytest.mark.parametrize("T", [np.float32, np.float64])
+@pytest.mark.parametrize("anchor", [N.ANCHOR_ZERO, N.ANCHOR_MIN])
+def test_zero_prev_against_every_kind_of_cur(T, anchor):
+    """p = +0 and -0 against x = +-0, +-1, +-inf, NaN, subnormal and huge values, spread among
+    ordinary points (one zero every 97 points): (x - p) / p is +-inf or NaN, never binnable,
+    whichever x; the kernels decide these points without dividing."""
+    rng = np.random.default_rng(41)
+    n = 20_000
+    p = rng.lognormal(size=n).astype(T)
+    x = (p * (T(1) + rng.normal(0, 1e-3, n))).astype(T)
+    fi = np.finfo(T)
+    xs = np.array([0.0, -0.0, 1.0, -1.0, np.inf, -np.inf, np.nan, fi.smallest_subnormal,
+                   -fi.smallest_subnormal, fi.max, -fi.max, 3.5], dtype=T)
+    idx = np.arange(0, n, 97)
+    p[idx] = np.where(np.arange(idx.size) % 2 == 0, T(0.0), T(-0.0))
+    x[idx] = xs[np.arange(idx.size) % xs.size]
+    h, _ = check_pair(p, x, 1e-3, 8, anchor=anchor, ranges=[(0, n), (95, 300)])
+    assert h["n_inc"] >= idx.size
+
+
 @pytest.mark.parametrize("B", [1, 2, 3, 5, 7, 8, 11, 13, 16])
 def test_all_widths_small_blocks(B):
     """Index widths whose blocks do not hold a multiple of 32 indices; many blocks and
