@@ -100,6 +100,9 @@ constexpr int K3_THREADS = K3_WARPS * 32;
 constexpr int K3_SEG = 128;                     // K3f's warp step: 4 consecutive points per lane
 constexpr int STEPS = SUB / 32;                 // 32-element ballot words per tile
 constexpr int K3_SMEM = 65536 * 2;              // index of every 16-bit code (bytes)
+// K3a's per-warp stage: one step's code vectors (32 lanes x up to 4, and lane 31's extra one)
+constexpr int K3A_STAGE_U4 = 32 * 4 + 1;
+constexpr int K3A_SMEM = K3_SMEM + K3_WARPS * K3A_STAGE_U4 * 16;
 
 // K3a — indexing and packing, from K1's codes alone. One warp processes one 4096-element tile at
 // a time (tile gw, gw + W, ... for global warp gw of W): index = rank of the code's bin if the
@@ -243,15 +246,41 @@ __device__ __forceinline__ void shifted_codes(const unsigned (&win)[NW + 4], int
 // per lane (a tile that starts off a 16-byte boundary funnel-shifts each lane's words with the
 // next lane's). Lanes past the tile end, or whose codes would reach past the codes array, read
 // their codes one by one.
+// Copies into the warp's stage (cp.async, one group) this lane's code vectors of the step at sb0
+// of tile t, those that lie inside the codes array, and for lane 31 of a tile that starts off a
+// 16-byte boundary the vector after them. A lane reads back only what it copied itself.
+template <int B>
+__device__ __forceinline__ void k3a_stage(const unsigned short* codes, const Geometry& g,
+                                          const TileRef& t, int sb0, uint4* stage, int lane) {
+  constexpr int EL = B % 2 == 0 ? 16 : 32, NV = EL / 8;
+  const int sh = (int)(t.j0 & 7);
+  const long long wb = t.j0 - sh;
+  const uint4* cw4 = reinterpret_cast<const uint4*>(codes + wb);
+  const int e0 = sb0 + EL * lane;
+  const long long w0 = wb + e0;
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+    if (w0 + 8 * (v + 1) <= g.n) cp_async16(stage + lane * NV + v, cw4 + (e0 >> 3) + v);
+  if (lane == 31 && sh && e0 + EL <= t.cnt && w0 + EL + 8 <= g.n)
+    cp_async16(stage + 32 * NV, cw4 + (e0 >> 3) + NV);
+  cp_async_commit();
+}
+
 // One tile gt (one warp): its packed indices, its incompressible flags as half-ballot words into
 // `halves` (u16 h: points 16 h .. 16 h + 15 of the tile; the tile's own code area, or any other
 // 512-byte buffer), and the return value: the tile's incompressible count, with K3_FAR_FLAG when
-// points outside the code window need K3f.
+// points outside the code window need K3f. With a stage (K3A_STAGE_U4 vectors of shared memory,
+// holding this tile's first step on entry), each step's codes come from the stage, and the next
+// step's (or the first step of tile next_gt, if >= 0) are copied in while the step is indexed.
+// (The flags of a step go to the first 256 codes of the tile, already consumed: the next step's
+// codes start SEGW >= 512 codes in.)
 template <int B, typename T>
 __device__ __forceinline__ unsigned long long k3a_tile(const AssignArgs<T>& A,
                                                        const unsigned short* s_tab, long long gt,
                                                        int lane, int any, bool far_chk,
-                                                       unsigned short* halves) {
+                                                       unsigned short* halves,
+                                                       uint4* stage = nullptr,
+                                                       long long next_gt = -1) {
   constexpr unsigned M = (1u << B) - 1u;
   constexpr bool kSentinel = B < 16;             // see k3_assign
   constexpr int EL = B % 2 == 0 ? 16 : 32, NW = EL / 2, NV = EL / 8, WL = EL * B / 32;
@@ -270,10 +299,11 @@ __device__ __forceinline__ unsigned long long k3a_tile(const AssignArgs<T>& A,
       const int e0 = sb0 + EL * lane;
       const long long w0 = wb + e0;              // this lane's first aligned code
       unsigned win[NW + 4];
+      if (stage) cp_async_wait_all();            // this step's group has landed
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         uint4 a = make_uint4(0u, 0u, 0u, 0u);
-        if (w0 + 8 * (v + 1) <= g.n) a = __ldcs(cw4 + (e0 >> 3) + v);
+        if (w0 + 8 * (v + 1) <= g.n) a = stage ? stage[lane * NV + v] : __ldcs(cw4 + (e0 >> 3) + v);
         win[4 * v] = a.x; win[4 * v + 1] = a.y; win[4 * v + 2] = a.z; win[4 * v + 3] = a.w;
       }
 #pragma unroll
@@ -281,8 +311,14 @@ __device__ __forceinline__ unsigned long long k3a_tile(const AssignArgs<T>& A,
       const bool inside = e0 + EL <= cnt;
       const bool whole = w0 + EL + (sh ? 8 : 0) <= g.n;
       if (lane == 31 && sh && inside && whole) {
-        const uint4 b = __ldcs(cw4 + (e0 >> 3) + NV);
+        const uint4 b = stage ? stage[32 * NV] : __ldcs(cw4 + (e0 >> 3) + NV);
         win[NW] = b.x; win[NW + 1] = b.y; win[NW + 2] = b.z; win[NW + 3] = b.w;
+      }
+      if (stage) {                               // the next step's codes, in flight meanwhile
+        if (sb0 + SEGW < cnt)
+          k3a_stage<B>(A.codes, g, tr, sb0 + SEGW, stage, lane);
+        else if (next_gt >= 0)
+          k3a_stage<B>(A.codes, g, tile_ref<B>(g, next_gt, A.blob, A.codes), 0, stage, lane);
       }
       unsigned cw[NW];
       if (inside && whole) {
@@ -373,14 +409,18 @@ __device__ __forceinline__ bool far_check(const Ctrl* ctrl, int any) {
 template <int B, typename T>
 __device__ __forceinline__ void k3a_tiles(const AssignArgs<T>& A, const unsigned short* s_tab,
                                           long long gt_begin, long long gt_end, long long W,
-                                          int lane, int any) {
+                                          int lane, int any, uint4* stage = nullptr) {
   const bool chk = far_check(A.ctrl, any);
+  if (stage && gt_begin < gt_end)
+    k3a_stage<B>(A.codes, A.g, tile_ref<B>(A.g, gt_begin, A.blob, A.codes), 0, stage, lane);
   for (long long gt = gt_begin; gt < gt_end; gt += W) {
     // the flags go over the tile's own, already consumed codes
     unsigned short* own = tile_ref<B>(A.g, gt, A.blob, A.codes).halves;
-    const unsigned long long st = k3a_tile<B>(A, s_tab, gt, lane, any, chk, own);
+    const long long next = gt + W < gt_end ? gt + W : -1;
+    const unsigned long long st = k3a_tile<B>(A, s_tab, gt, lane, any, chk, own, stage, next);
     if (lane == 0) A.tstatus[gt] = st;
   }
+  if (stage) cp_async_wait_all();   // (nothing is left in flight: the last step stages nothing)
 }
 
 // K3a's table of the index of every 16-bit code, built by all threads of the CTA (ends with a
@@ -408,12 +448,14 @@ __device__ __forceinline__ void k3a_table(const AssignArgs<T>& A, unsigned short
 
 template <typename T, int B>
 __global__ void __launch_bounds__(K3_THREADS, 1) k3_assign(AssignArgs<T> A) {
-  extern __shared__ __align__(16) unsigned short s_tab[];   // [65536]: index of each code
+  extern __shared__ __align__(16) unsigned short s_tab[];   // [65536]: index of each code, then
+  uint4* stage = reinterpret_cast<uint4*>(s_tab + 65536) +   // the warps' stages
+                 (threadIdx.x >> 5) * K3A_STAGE_U4;
   const int any = A.ctrl->any;
   k3a_table<T, B>(A, s_tab, any);   // the only block-wide barriers
   const long long W = (long long)gridDim.x * K3_WARPS;
   k3a_tiles<B>(A, s_tab, (long long)blockIdx.x * K3_WARPS + (threadIdx.x >> 5), A.g.nsub, W,
-               (int)lane_id(), any);
+               (int)lane_id(), any, stage);
 }
 
 // K3f — tiles with points outside K1's code window (flagged by K3a; rare: a bin more than 16383
@@ -881,9 +923,9 @@ static cudaError_t launch_assign_t(const CompressPlan& P, cudaStream_t s, const 
   cudaGetDevice(&dev);
   int per_sm = dev < 64 ? occ[dev][P.g.B] : 0;
   if (per_sm == 0) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, K3_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, K3A_SMEM);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, K3_THREADS, K3_SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, K3_THREADS, K3A_SMEM);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     if (dev < 64) occ[dev][P.g.B] = per_sm;
@@ -891,7 +933,7 @@ static cudaError_t launch_assign_t(const CompressPlan& P, cudaStream_t s, const 
   long long blocks = (long long)P.sms * per_sm;
   const long long need = (P.g.nsub + K3_WARPS - 1) / K3_WARPS;
   if (blocks > need) blocks = need;
-  fn<<<(int)blocks, K3_THREADS, K3_SMEM, s>>>(A);
+  fn<<<(int)blocks, K3_THREADS, K3A_SMEM, s>>>(A);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // K3f: tiles with points outside the code window (usually none; the kernel only reads flags)
