@@ -776,7 +776,8 @@ __device__ __forceinline__ void k3_fused_part(const AssignArgs<T>& A, long long 
   const int any = A.ctrl->any;
   const int lane = (int)lane_id(), warp = (int)(threadIdx.x >> 5);
   k3a_table<T, B>(A, s_tab, any);
-  k3a_tiles<B>(A, s_tab, t0 + warp, t1, K3_WARPS, lane, any);
+  uint4* stage = reinterpret_cast<uint4*>(s_tab + 65536) + warp * K3A_STAGE_U4;
+  k3a_tiles<B>(A, s_tab, t0 + warp, t1, K3_WARPS, lane, any, stage);
   __syncwarp();      // the tile counts (and flags) lane 0 stored are visible to the warp
   if (!any) return;
   Consts<T> c = A.c;
@@ -802,7 +803,7 @@ __device__ __forceinline__ void k3_fused_dispatch(const AssignArgs<T>& A, long l
 
 // CTA b of G takes tiles [b NT / G, (b + 1) NT / G) of the list, variable by variable.
 __global__ void __launch_bounds__(K3_THREADS, 1) k3_assign_fused(FusedArgs F) {
-  extern __shared__ __align__(16) unsigned short s_tab[];   // [65536]: index of each code
+  extern __shared__ __align__(16) unsigned short s_tab[];   // [65536]: index of each code, stages
   __shared__ AssignArgs<double> s_ad;
   __shared__ AssignArgs<float> s_af;
   const long long G = gridDim.x, b = blockIdx.x;
@@ -997,9 +998,9 @@ cudaError_t launch_fused_assign(const FusedArgs& F, int sms, cudaStream_t s) {
   int per_sm = dev < 64 ? occ[dev] : 0;
   if (per_sm == 0) {
     cudaError_t e = cudaFuncSetAttribute(k3_assign_fused,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, K3_SMEM);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, K3A_SMEM);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_assign_fused, K3_THREADS, K3_SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_assign_fused, K3_THREADS, K3A_SMEM);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     if (dev < 64) occ[dev] = per_sm;
@@ -1007,7 +1008,7 @@ cudaError_t launch_fused_assign(const FusedArgs& F, int sms, cudaStream_t s) {
   long long blocks = (long long)sms * per_sm;
   const long long need = (F.NT + K3_WARPS - 1) / K3_WARPS;
   if (blocks > need) blocks = need;
-  k3_assign_fused<<<(int)blocks, K3_THREADS, K3_SMEM, s>>>(F);
+  k3_assign_fused<<<(int)blocks, K3_THREADS, K3A_SMEM, s>>>(F);
   return cudaGetLastError();
 }
 
