@@ -115,6 +115,47 @@ __host__ __forceinline__ int seg_log2_for(long long tiles, long long resident_wa
   return s;
 }
 
+// Four consecutive values from shared memory (16-byte aligned).
+__device__ __forceinline__ void lds4(const double* p, double* v) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0];
+  const double2 b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void lds4(const float* p, float* v) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+
+// K4's per-warp stage (float64, B <= K4_STAGE_MAX_B): a step's 128 prev values, then its 16 B
+// bytes of index field.
+constexpr int K4_STAGE_MAX_B = 10;
+constexpr int K4_STAGE_FIELD = K4_SEG * 8;
+constexpr int K4_STAGE_BYTES = K4_STAGE_FIELD + 16 * K4_STAGE_MAX_B;
+
+// load_field for a staged step: the 4B-bit field of lane `lane` from the step's own 4B words.
+template <int B>
+__device__ __forceinline__ typename Field<B>::type load_field_staged(const unsigned* sw, int lane) {
+  constexpr int FB = 4 * B;
+  constexpr int NW = B * 4;                      // words of one step's image
+  using F = typename Field<B>::type;
+  if constexpr (FB == 32) {
+    return sw[lane];
+  } else {
+    static_assert(FB < 64, "staged steps have B <= 10");
+    const int bit = FB * lane;
+    const int w0 = bit >> 5, o = bit & 31;
+    const unsigned a0 = sw[w0];
+    const unsigned a1 = (o + FB > 32 && w0 + 1 < NW) ? sw[w0 + 1] : 0u;
+    const unsigned long long v = (unsigned long long)a0 | ((unsigned long long)a1 << 32);
+    if constexpr (FB > 32) {
+      const unsigned a2 = (o + FB > 64 && w0 + 2 < NW) ? sw[w0 + 2] : 0u;
+      return (F)((v >> o) | (o ? ((unsigned long long)a2 << (64 - o)) : 0ull));
+    } else {
+      return (F)(v >> o);
+    }
+  }
+}
+
 // Number of incompressible points (fields equal to the marker M) among the first e_end points
 // of a sub-block (e_end a multiple of K4_SEG, at most its point count cnt); warp-uniform.
 template <int B>

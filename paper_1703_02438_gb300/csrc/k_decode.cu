@@ -26,12 +26,32 @@ namespace nmk {
 
 namespace {
 
+// Starts the copies of the whole step at s1 (16-byte aligned prev and tile image tw) into the
+// warp's stage wst: this lane's four prev values and (lanes 0 .. B-1) the step's 16 B bytes of
+// index field.
+template <int B>
+__device__ __forceinline__ void k4_stage(unsigned char* wst, const double* pt, int s1, int lane,
+                                         const unsigned* tw) {
+  double* sp = reinterpret_cast<double*>(wst);
+  const int e = s1 + 4 * lane;
+  cp_async16(sp + 4 * lane, pt + e);
+  cp_async16(sp + 4 * lane + 2, pt + e + 2);
+  if (lane < B)
+    cp_async16(wst + K4_STAGE_FIELD + 16 * lane,
+               reinterpret_cast<const unsigned char*>(tw) + (s1 / K4_SEG) * 16 * B + 16 * lane);
+  cp_async_commit();
+}
+
 // Decodes units u_begin, u_begin + W, ... < u_end (unit u: segment u mod 2^seg_log2 of tile
-// u >> seg_log2), one warp.
+// u >> seg_log2), one warp. With stages (float64, B <= K4_STAGE_MAX_B: K4_STAGE_BYTES of shared
+// memory per warp of the CTA) a warp copies the next step's prev values and index field into its
+// stage as soon as it has read the current step's, so that they travel while the current step
+// waits for its incompressible values.
 template <typename T, int B>
 __device__ __forceinline__ void decode_tiles(const DecodeArgs& A, const Geometry& g,
                                              long long n_inc, long long u_begin, long long u_end,
-                                             long long W, const T* s_m) {
+                                             long long W, const T* s_m,
+                                             unsigned char* stages = nullptr) {
   using U = typename BitsOf<T>::U;
   using F = typename Field<B>::type;
   constexpr int FB = 4 * B;
@@ -76,6 +96,56 @@ __device__ __forceinline__ void decode_tiles(const DecodeArgs& A, const Geometry
     const bool vec = e_lo == 0 && ((reinterpret_cast<uintptr_t>(pt) |
                                     reinterpret_cast<uintptr_t>(ot)) & 15) == 0;
     long long run = base + (sbeg ? markers_before<B>(tw, twords, cnt, sbeg, lane) : 0u);
+    if constexpr (sizeof(T) == 8 && B <= K4_STAGE_MAX_B) {
+      if (stages && vec && (reinterpret_cast<uintptr_t>(tw) & 15) == 0) {
+        unsigned char* wst = stages + (threadIdx.x >> 5) * K4_STAGE_BYTES;
+        const double* sp = reinterpret_cast<const double*>(wst);
+        const unsigned* sw = reinterpret_cast<const unsigned*>(wst + K4_STAGE_FIELD);
+        const double* ptd = reinterpret_cast<const double*>(pt);
+        bool staged = false;                     // this step's inputs are in the stage
+        for (int s0 = sbeg; s0 < send; s0 += K4_SEG) {
+          const int e0 = s0 + 4 * lane;
+          const bool whole = s0 + K4_SEG <= e_hi;
+          F field;
+          T pv[4];
+          if (staged) {
+            cp_async_wait_all();
+            __syncwarp();                        // the field words other lanes copied
+            field = load_field_staged<B>(sw, lane);
+            lds4(sp + 4 * lane, pv);
+          } else if (whole) {
+            field = load_field<B>(tw, twords, (s0 / K4_SEG) * FB, lane);
+            ld4(pt + e0, pv);
+          } else {
+            field = load_field<B>(tw, twords, (s0 / K4_SEG) * FB, lane);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) pv[k] = e0 + k < e_hi ? __ldcs(pt + e0 + k) : (T)0;
+          }
+          staged = false;
+          const int s1 = s0 + K4_SEG;
+          if (s1 < send && s1 + K4_SEG <= e_hi) {
+            __syncwarp();                        // every lane has read this step's field
+            k4_stage<B>(wst, ptd, s1, lane, tw);
+            staged = true;
+          }
+          T r[4];
+          run += decode_step<T, B>(field, pv, e0, cnt, e_lo, e_hi, run, lt, s_m, centres, exact_u,
+                                   n_inc, A, r);
+          if (whole) {
+            st4(ot + e0, r);
+          } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              if (e0 + k < e_hi) ot[e0 + k] = r[k];
+          }
+        }
+        if (send == cnt && lane == 0) {         // this warp ends the tile: all its markers seen
+          const long long next = (gt + 1 < g.nsub) ? sub_off[gt + 1] : n_inc;
+          if (run != next) report(A, NUMARCK_ERR_CORRUPT);
+        }
+        continue;
+      }
+    }
     for (int s0 = sbeg; s0 < send; s0 += K4_SEG * k4_unroll<T>()) {
       F field[k4_unroll<T>()];
       T pv[k4_unroll<T>()][4];
@@ -120,17 +190,21 @@ __device__ __forceinline__ void decode_tiles(const DecodeArgs& A, const Geometry
 template <typename T, int B = 1>
 __device__ __forceinline__ void decode_dispatch(const DecodeArgs& A, const Geometry& g,
                                                 long long n_inc, long long u_begin,
-                                                long long u_end, long long W, const T* s_m) {
+                                                long long u_end, long long W, const T* s_m,
+                                                unsigned char* stages = nullptr) {
   if constexpr (B <= NUMARCK_MAX_B) {
     if (g.B == B)
-      decode_tiles<T, B>(A, g, n_inc, u_begin, u_end, W, s_m);
+      decode_tiles<T, B>(A, g, n_inc, u_begin, u_end, W, s_m, stages);
     else
-      decode_dispatch<T, B + 1>(A, g, n_inc, u_begin, u_end, W, s_m);
+      decode_dispatch<T, B + 1>(A, g, n_inc, u_begin, u_end, W, s_m, stages);
   }
 }
 
+constexpr int K4_DSMEM = K4_WARPS * K4_STAGE_BYTES;   // k4_decode's dynamic shared memory
+
 __global__ void __launch_bounds__(K4_THREADS, 2) k4_decode(DecodeArgs A) {
   __shared__ __align__(16) unsigned char s_tab[DM_SMEM * 8];   // multipliers m = 1 + centre
+  extern __shared__ __align__(16) unsigned char k4_stages[];   // the warps' stages
   __shared__ __align__(16) numarck_header s_h;
   __shared__ Geometry s_g;
   __shared__ long long s_g0, s_g1;
@@ -172,7 +246,7 @@ __global__ void __launch_bounds__(K4_THREADS, 2) k4_decode(DecodeArgs A) {
     const double* centres = reinterpret_cast<const double*>(A.blob + g.off_centres);
     for (int r = threadIdx.x; r < nm; r += K4_THREADS) s_m[r] = t_add(1.0, centres[r]);
     __syncthreads();   // the only block-wide barrier after the header
-    decode_dispatch<double>(A, g, s_h.n_inc, u0, u1, W, s_m);
+    decode_dispatch<double>(A, g, s_h.n_inc, u0, u1, W, s_m, k4_stages);
   } else {
     float* s_m = reinterpret_cast<float*>(s_tab);
     const float* centres = reinterpret_cast<const float*>(A.blob + g.off_centres);
@@ -307,7 +381,10 @@ cudaError_t launch_decode(const DecodePlan& P, cudaStream_t s) {
   cudaGetDevice(&dev);
   int per_sm = dev < 64 ? occ[dev] : 0;
   if (per_sm == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k4_decode, K4_THREADS, 0);
+    cudaError_t e = cudaFuncSetAttribute(k4_decode, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         K4_DSMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k4_decode, K4_THREADS, K4_DSMEM);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     if (dev < 64) occ[dev] = per_sm;
@@ -323,7 +400,7 @@ cudaError_t launch_decode(const DecodePlan& P, cudaStream_t s) {
   }
   DecodeArgs A{P.blob, P.prev_seg, P.out_seg, P.status, P.start, P.count, P.n_expected, P.status2,
                P.dtype, sl};
-  k4_decode<<<(int)blocks, K4_THREADS, 0, s>>>(A);
+  k4_decode<<<(int)blocks, K4_THREADS, K4_DSMEM, s>>>(A);
   return cudaGetLastError();
 }
 

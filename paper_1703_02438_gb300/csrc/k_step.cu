@@ -49,15 +49,6 @@ struct Stage {
 };
 
 
-__device__ __forceinline__ void lds4(const double* p, double* v) {
-  const double2 a = reinterpret_cast<const double2*>(p)[0];
-  const double2 b = reinterpret_cast<const double2*>(p)[1];
-  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-}
-__device__ __forceinline__ void lds4(const float* p, float* v) {
-  const float4 a = *reinterpret_cast<const float4*>(p);
-  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-}
 
 // Starts the copies of the whole step at s1 (16-byte aligned inputs and tile image tw) into the
 // warp's stage wst: this lane's four prev and four cur values, and (lanes 0 .. B-1) the step's
@@ -78,30 +69,6 @@ __device__ __forceinline__ void stage_step(unsigned char* wst, const T* pt, cons
     cp_async16(wst + Stage<T>::FIELD + 16 * lane,
                reinterpret_cast<const unsigned char*>(tw) + (s1 / K4_SEG) * 16 * B + 16 * lane);
   cp_async_commit();
-}
-
-// load_field for a staged step: the 4B-bit field of lane `lane` from the step's own 4B words.
-template <int B>
-__device__ __forceinline__ typename Field<B>::type load_field_staged(const unsigned* sw, int lane) {
-  constexpr int FB = 4 * B;
-  constexpr int NW = B * 4;                      // words of one step's image
-  using F = typename Field<B>::type;
-  if constexpr (FB == 32) {
-    return sw[lane];
-  } else {
-    static_assert(FB < 64, "staged steps have B <= 10");
-    const int bit = FB * lane;
-    const int w0 = bit >> 5, o = bit & 31;
-    const unsigned a0 = sw[w0];
-    const unsigned a1 = (o + FB > 32 && w0 + 1 < NW) ? sw[w0 + 1] : 0u;
-    const unsigned long long v = (unsigned long long)a0 | ((unsigned long long)a1 << 32);
-    if constexpr (FB > 32) {
-      const unsigned a2 = (o + FB > 64 && w0 + 2 < NW) ? sw[w0 + 2] : 0u;
-      return (F)((v >> o) | (o ? ((unsigned long long)a2 << (64 - o)) : 0ull));
-    } else {
-      return (F)(v >> o);
-    }
-  }
 }
 
 struct StepArgs {
