@@ -126,11 +126,12 @@ __device__ __forceinline__ void lds4(const float* p, float* v) {
   v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
 }
 
-// K4's per-warp stage (float64, B <= K4_STAGE_MAX_B): a step's 128 prev values, then its 16 B
-// bytes of index field.
+// K4's per-warp stage (B <= K4_STAGE_MAX_B): a step's 128 prev values, then its 16 B bytes of
+// index field (K4_STAGE_BYTES: room for float64).
 constexpr int K4_STAGE_MAX_B = 10;
-constexpr int K4_STAGE_FIELD = K4_SEG * 8;
-constexpr int K4_STAGE_BYTES = K4_STAGE_FIELD + 16 * K4_STAGE_MAX_B;
+template <typename T>
+__host__ __device__ constexpr int k4_stage_field() { return K4_SEG * (int)sizeof(T); }
+constexpr int K4_STAGE_BYTES = K4_SEG * 8 + 16 * K4_STAGE_MAX_B;
 
 // load_field for a staged step: the 4B-bit field of lane `lane` from the step's own 4B words.
 template <int B>

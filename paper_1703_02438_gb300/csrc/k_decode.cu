@@ -29,22 +29,23 @@ namespace {
 // Starts the copies of the whole step at s1 (16-byte aligned prev and tile image tw) into the
 // warp's stage wst: this lane's four prev values and (lanes 0 .. B-1) the step's 16 B bytes of
 // index field.
-template <int B>
-__device__ __forceinline__ void k4_stage(unsigned char* wst, const double* pt, int s1, int lane,
+template <typename T, int B>
+__device__ __forceinline__ void k4_stage(unsigned char* wst, const T* pt, int s1, int lane,
                                          const unsigned* tw) {
-  double* sp = reinterpret_cast<double*>(wst);
+  constexpr int PER = 16 / (int)sizeof(T);       // values per 16-byte copy
+  T* sp = reinterpret_cast<T*>(wst);
   const int e = s1 + 4 * lane;
-  cp_async16(sp + 4 * lane, pt + e);
-  cp_async16(sp + 4 * lane + 2, pt + e + 2);
+#pragma unroll
+  for (int c = 0; c < 4 / PER; ++c) cp_async16(sp + 4 * lane + c * PER, pt + e + c * PER);
   if (lane < B)
-    cp_async16(wst + K4_STAGE_FIELD + 16 * lane,
+    cp_async16(wst + k4_stage_field<T>() + 16 * lane,
                reinterpret_cast<const unsigned char*>(tw) + (s1 / K4_SEG) * 16 * B + 16 * lane);
   cp_async_commit();
 }
 
 // Decodes units u_begin, u_begin + W, ... < u_end (unit u: segment u mod 2^seg_log2 of tile
-// u >> seg_log2), one warp. With stages (float64, B <= K4_STAGE_MAX_B: K4_STAGE_BYTES of shared
-// memory per warp of the CTA) a warp copies the next step's prev values and index field into its
+// u >> seg_log2), one warp. With stages (B <= K4_STAGE_MAX_B: K4_STAGE_BYTES of shared memory
+// per warp of the CTA) a warp copies the next step's prev values and index field into its
 // stage as soon as it has read the current step's, so that they travel while the current step
 // waits for its incompressible values.
 template <typename T, int B>
@@ -96,12 +97,11 @@ __device__ __forceinline__ void decode_tiles(const DecodeArgs& A, const Geometry
     const bool vec = e_lo == 0 && ((reinterpret_cast<uintptr_t>(pt) |
                                     reinterpret_cast<uintptr_t>(ot)) & 15) == 0;
     long long run = base + (sbeg ? markers_before<B>(tw, twords, cnt, sbeg, lane) : 0u);
-    if constexpr (sizeof(T) == 8 && B <= K4_STAGE_MAX_B) {
+    if constexpr (B <= K4_STAGE_MAX_B) {
       if (stages && vec && (reinterpret_cast<uintptr_t>(tw) & 15) == 0) {
         unsigned char* wst = stages + (threadIdx.x >> 5) * K4_STAGE_BYTES;
-        const double* sp = reinterpret_cast<const double*>(wst);
-        const unsigned* sw = reinterpret_cast<const unsigned*>(wst + K4_STAGE_FIELD);
-        const double* ptd = reinterpret_cast<const double*>(pt);
+        const T* sp = reinterpret_cast<const T*>(wst);
+        const unsigned* sw = reinterpret_cast<const unsigned*>(wst + k4_stage_field<T>());
         bool staged = false;                     // this step's inputs are in the stage
         for (int s0 = sbeg; s0 < send; s0 += K4_SEG) {
           const int e0 = s0 + 4 * lane;
@@ -125,7 +125,7 @@ __device__ __forceinline__ void decode_tiles(const DecodeArgs& A, const Geometry
           const int s1 = s0 + K4_SEG;
           if (s1 < send && s1 + K4_SEG <= e_hi) {
             __syncwarp();                        // every lane has read this step's field
-            k4_stage<B>(wst, ptd, s1, lane, tw);
+            k4_stage<T, B>(wst, pt, s1, lane, tw);
             staged = true;
           }
           T r[4];
@@ -200,7 +200,7 @@ __device__ __forceinline__ void decode_dispatch(const DecodeArgs& A, const Geome
   }
 }
 
-constexpr int K4_DSMEM = K4_WARPS * K4_STAGE_BYTES;   // k4_decode's dynamic shared memory
+constexpr int K4_DSMEM = K4_WARPS * K4_STAGE_BYTES;   // K4 kernels: dynamic shared memory
 
 __global__ void __launch_bounds__(K4_THREADS, 2) k4_decode(DecodeArgs A) {
   __shared__ __align__(16) unsigned char s_tab[DM_SMEM * 8];   // multipliers m = 1 + centre
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(K4_THREADS, 2) k4_decode(DecodeArgs A) {
     const float* centres = reinterpret_cast<const float*>(A.blob + g.off_centres);
     for (int r = threadIdx.x; r < nm; r += K4_THREADS) s_m[r] = t_add(1.0f, centres[r]);
     __syncthreads();
-    decode_dispatch<float>(A, g, s_h.n_inc, u0, u1, W, s_m);
+    decode_dispatch<float>(A, g, s_h.n_inc, u0, u1, W, s_m, k4_stages);
   }
 }
 
@@ -318,6 +318,7 @@ constexpr int K4_CHUNK = 4 * K4_WARPS;
 
 __global__ void __launch_bounds__(K4_THREADS, 2) k4_fused(FusedDecodeArgs D) {
   __shared__ __align__(16) unsigned char s_tab[DM_SMEM * 8];   // multipliers m = 1 + centre
+  extern __shared__ __align__(16) unsigned char k4_stages[];   // the warps' stages
   __shared__ __align__(16) numarck_header s_h;
   __shared__ Geometry s_g;
   __shared__ DecodeArgs s_a;
@@ -364,10 +365,10 @@ __global__ void __launch_bounds__(K4_THREADS, 2) k4_fused(FusedDecodeArgs D) {
       const long long u0 = (t0 << D.seg_log2) + (threadIdx.x >> 5), u1 = t1 << D.seg_log2;
       if (s_g.dtype == NUMARCK_F64)
         decode_dispatch<double>(s_a, s_g, s_h.n_inc, u0, u1, K4_WARPS,
-                                reinterpret_cast<const double*>(s_tab));
+                                reinterpret_cast<const double*>(s_tab), k4_stages);
       else
         decode_dispatch<float>(s_a, s_g, s_h.n_inc, u0, u1, K4_WARPS,
-                               reinterpret_cast<const float*>(s_tab));
+                               reinterpret_cast<const float*>(s_tab), k4_stages);
     }
   }
 }
@@ -411,7 +412,10 @@ cudaError_t launch_fused_decode(const FusedDecodeArgs& D, int sms, cudaStream_t 
   cudaGetDevice(&dev);
   int per_sm = dev < 64 ? occ[dev] : 0;
   if (per_sm == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k4_fused, K4_THREADS, 0);
+    cudaError_t e = cudaFuncSetAttribute(k4_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         K4_DSMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k4_fused, K4_THREADS, K4_DSMEM);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     if (dev < 64) occ[dev] = per_sm;
@@ -419,7 +423,7 @@ cudaError_t launch_fused_decode(const FusedDecodeArgs& D, int sms, cudaStream_t 
   k4_fused_prep<<<1, KP_THREADS, 0, s>>>(D);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k4_fused<<<sms * per_sm, K4_THREADS, 0, s>>>(D);
+  k4_fused<<<sms * per_sm, K4_THREADS, K4_DSMEM, s>>>(D);
   return cudaGetLastError();
 }
 
