@@ -94,7 +94,7 @@ Consts<T> make_consts(double E, int anchor) {
   c.inv_wf = (float)c.inv_w;
   c.Ef = (float)c.E_T;
   c.wf = (float)c.w;
-  c.cap_lo = f_down((double)c.cap * (1.0 - 0x1p-19));
+  c.cap_lo = f_down(std::fmin((double)c.cap * (1.0 - 0x1p-19), 0x1p100));
   c.cap_hi = f_up((double)c.cap * (1.0 + 0x1p-19));
   c.K0 = f_up(0x1p-19 * (double)c.inv_w * std::fabs((double)c.a) + 0x1p-60);
   c.kA = f_up((0x1p-22 + 0x1p-23 + 0x1p-50) * (1.0 + 0x1p-40));

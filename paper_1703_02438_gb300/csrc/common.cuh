@@ -180,7 +180,7 @@ struct Consts {
   T E_T, w, inv_w, cap, a;
   int hbase;      // histogram window index = bin - hbase
   // float64 estimate: af = fl32(a), inv_wf = fl32(inv_w), Ef = fl32(E_T), wf = fl32(w),
-  // cap_lo <= cap (1 - 2^-19), cap_hi >= cap (1 + 2^-19),
+  // cap_lo <= min(cap (1 - 2^-19), 2^100), cap_hi >= cap (1 + 2^-19),
   // K0 >= 2^-19 inv_w |a| + 2^-60, and for K1's own-bin check kA >= 2^-22 + 2^-23 + 2^-50,
   // k1 >= 2^-20 (1 + Ef), C0 >= 2^-22 |af| + 2^-49 + 2^-50 + 2^-100 (all rounded away from
   // the decision)
@@ -495,7 +495,9 @@ __device__ __forceinline__ int classify_check_f64_fast(double p, double x, const
   const bool yes = __fmaf_ru(aG, 0x1.000002p+0f, T1) < __fmul_rd(H, 0x1.fffffp-1f);
   const bool no = __fmul_rd(aG, 0x1.fffffcp-1f) > __fmaf_ru(H, 0x1.000008p+0f, T1);
   pass = yes;
-  const bool in_range = (unsigned)(ep - 200) <= 1740u && ex != 0x7FF;   // estimate valid
+  // estimate valid (a non-finite x gives |Df| >= 2^106 or est false: beyond cap_lo, which is at
+  // most 2^100 and, with E < 1, below 2^22)
+  const bool in_range = (unsigned)(ep - 200) <= 1740u;
   // binnable with its bin decided: the estimate is valid and finite, certainly within the cap,
   // and both ends of its error interval fall in one bin
   const bool sure = in_range && est && aD <= c.cap_lo && lo == hi && lo < 4194304.0f;

@@ -93,6 +93,14 @@ def guard_pair(E=1e-3, per=2000, seed=71):
             p = _scaled(rng, per // 4, e)
             ps.append(p)
             xs.append(p.copy())
+        # non-finite x against p whose biased exponent is 1920..1940, where x - p = +-inf or NaN
+        # still passes the estimate's exponent test: its size (>= 2^106) must keep it out
+        nanbits = np.array([0x7FF8000000000000, 0x7FF0000000000001, 0xFFF4000000000ABC],
+                           dtype=np.uint64).view(np.float64)
+        specials = np.concatenate([[np.inf, -np.inf], nanbits])
+        p = _scaled(rng, per, rng.integers(1920, 1941, per))
+        ps.append(p)
+        xs.append(specials[rng.integers(0, specials.size, per)])
         bits = (rng.integers(0, 2047, 4 * per).astype(np.uint64) << np.uint64(52)) | \
             rng.integers(0, 1 << 52, 4 * per, dtype=np.uint64)
         p = bits.view(np.float64) * rng.choice([-1.0, 1.0], 4 * per)
@@ -117,6 +125,8 @@ def test_guard_inputs_reach_both_sides():
     for e in (99, 100, 101, 1940, 1941):
         assert (ex == e).sum() >= 500, e
     assert ((ep == 0) & (p != 0)).any() and ((ex == 0) & (x != 0)).any()   # subnormals
+    high = (ep >= 1920) & (ep <= 1940)
+    assert (high & np.isinf(x)).sum() >= 500 and (high & np.isnan(x)).sum() >= 500
     with np.errstate(all="ignore"):
         q = np.abs(x / p)
     assert ((q > 2.0 ** 125) & (q < 2.0 ** 130)).sum() >= 1000
