@@ -648,6 +648,13 @@ def run_served(args):
     offered = sum(v[1] for v in info.values()) / args.serve_seconds / 1e9
     allv = lat["compress"] + lat["decompress"]
     pct = lambda v, q: float(np.percentile(v, q)) if v else None
+    # where the time goes: waiting for a slot (and for the series' earlier requests, and for
+    # arena space) against running on a slot; and the latency of large against small requests
+    wait = [(c["t_start"] - c["t_submit"]) * 1e3 for c in ok]
+    run_ = [(c["t_end"] - c["t_start"]) * 1e3 for c in ok]
+    big = [(c["t_end"] - c["t_submit"]) * 1e3 for c in ok if info[c["id"]][1] >= (1 << 30)]
+    small = [(c["t_end"] - c["t_submit"]) * 1e3 for c in ok if info[c["id"]][1] < (64 << 20)]
+    worst = sorted(ok, key=lambda c: c["t_end"] - c["t_submit"])[-max(1, len(ok) // 100):]
     line = {"metric": "served compress/decompress requests: latency p50/p99 and aggregate input GB/s",
             "value": moved / span / 1e9, "unit": "GB/s", "n_gpus": 1,
             "higher_is_better": True, "data": "synthetic",
@@ -666,6 +673,20 @@ def run_served(args):
             "compress_p50_ms": pct(lat["compress"], 50), "compress_p99_ms": pct(lat["compress"], 99),
             "decompress_p50_ms": pct(lat["decompress"], 50),
             "decompress_p99_ms": pct(lat["decompress"], 99),
+            "breakdown": {
+                "wait_p50_ms": pct(wait, 50), "wait_p99_ms": pct(wait, 99),
+                "run_p50_ms": pct(run_, 50), "run_p99_ms": pct(run_, 99),
+                "ge_1GB_requests": len(big), "ge_1GB_p50_ms": pct(big, 50),
+                "ge_1GB_p99_ms": pct(big, 99),
+                "lt_64MB_requests": len(small), "lt_64MB_p50_ms": pct(small, 50),
+                "lt_64MB_p99_ms": pct(small, 99),
+                "slowest_1pct": {"count": len(worst),
+                                 "mean_wait_ms": float(np.mean([(c["t_start"] - c["t_submit"]) * 1e3
+                                                                for c in worst])),
+                                 "mean_run_ms": float(np.mean([(c["t_end"] - c["t_start"]) * 1e3
+                                                               for c in worst])),
+                                 "mean_input_mb": float(np.mean([info[c["id"]][1]
+                                                                 for c in worst])) / 1e6}},
             "server": {k: st[k] for k in ("deferred_memory", "arena_peak", "max_inflight")}}
     print(json.dumps(line), flush=True)
 
