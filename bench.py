@@ -655,6 +655,8 @@ def run_served(args):
     big = [(c["t_end"] - c["t_submit"]) * 1e3 for c in ok if info[c["id"]][1] >= (1 << 30)]
     small = [(c["t_end"] - c["t_submit"]) * 1e3 for c in ok if info[c["id"]][1] < (64 << 20)]
     worst = sorted(ok, key=lambda c: c["t_end"] - c["t_submit"])[-max(1, len(ok) // 100):]
+    t_first = min(c["t_submit"] for c in ok) if ok else 0.0
+    late = [(c["t_end"] - c["t_submit"]) * 1e3 for c in ok if c["t_submit"] >= t_first + 5.0]
     line = {"metric": "served compress/decompress requests: latency p50/p99 and aggregate input GB/s",
             "value": moved / span / 1e9, "unit": "GB/s", "n_gpus": 1,
             "higher_is_better": True, "data": "synthetic",
@@ -680,7 +682,11 @@ def run_served(args):
                 "ge_1GB_p99_ms": pct(big, 99),
                 "lt_64MB_requests": len(small), "lt_64MB_p50_ms": pct(small, 50),
                 "lt_64MB_p99_ms": pct(small, 99),
+                "after_5s_requests": len(late), "after_5s_p50_ms": pct(late, 50),
+                "after_5s_p99_ms": pct(late, 99),
                 "slowest_1pct": {"count": len(worst),
+                                 "mean_submit_s": float(np.mean([c["t_submit"] - t_first
+                                                                 for c in worst])),
                                  "mean_wait_ms": float(np.mean([(c["t_start"] - c["t_submit"]) * 1e3
                                                                 for c in worst])),
                                  "mean_run_ms": float(np.mean([(c["t_end"] - c["t_start"]) * 1e3
