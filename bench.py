@@ -1171,7 +1171,12 @@ def main():
             "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": _traffic(dominant, side),
-                         "algorithmic_bytes_per_launch": alg[dominant]},
+                         "algorithmic_bytes_per_launch": alg[dominant],
+                         # the same fractions of the peak for the whole step and for a
+                         # compression alone (also given below, outside this object)
+                         "step_frac": step_alg / (ms_step / 1e3) / 1e9 / peak,
+                         "compress_path_frac": comp_alg / (t_comp / 1e3) / 1e9 / peak,
+                         "compress_one_pass_frac": one_pass / (t_comp / 1e3) / 1e9 / peak},
             "kernels_ms": kernel_ms, "kernels_gbs": kernel_gbs, "launches_per_step": launches,
             "step_hbm_frac": step_alg / (ms_step / 1e3) / 1e9 / peak,
             "compress_gbs": n * L / (t_comp / 1e3) / 1e9,
